@@ -1,0 +1,315 @@
+"""Benchmark of the iALS++ epoch on GB300 (one JSON line on stdout).
+
+A step is one epoch of Algorithm 3 (residual recompute, then for every block
+the user pass and the item pass) over the ML20M-shaped synthetic workload:
+136,000 users x 20,000 items, 10M binary positives (Zipf(1.05) items,
+lognormal(3.7, 1.1) user lengths clipped to [5, 8000]), d = 128, b = 32,
+alpha0 = 0.1, lambda = 1e-3 scaled by (1 + nu |S_r|) with nu = 1.
+
+Metric: row-block solves per second, (|U| + |I|) * d / b per epoch.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp32|bf16] [--no-cpu-baseline]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+project: the paper ships no code) on a bounded sample of the same workload.
+Under torchrun each rank trains an independent replica on its own GPU
+(replicas only; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "ml20m_136k"
+WORKLOAD_DESC = ("ML20M-shaped synthetic: 136,000 users x 20,000 items, 10,000,000 positives, "
+                 "Zipf(1.05) items, lognormal(3.7,1.1) lengths in [5,8000], d=128, b=32, "
+                 "alpha0=0.1, lambda=1e-3, nu=1, seed 0")
+METRIC = "iALS++ epoch throughput (row-block solves/s = (|U|+|I|)*d/b per epoch)"
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- CPU oracle sample
+def oracle_sample(prob, frac=0.1):
+    """The FP64 oracle on the first `frac` of the users (all items): one user and
+    one item block step per call.  Returns (callable, rows per call)."""
+    import oracle
+    from paper_2110_14044_gb300 import synth
+    data = prob.data
+    n_sub = max(1, int(data.n_users * frac))
+    end = int(data.u_indptr[n_sub])
+    u_ptr = data.u_indptr[:n_sub + 1].copy()
+    u_idx = data.u_items[:end].copy()
+    i_ptr, i_idx = synth.transpose_csr(n_sub, data.n_items, u_ptr, u_idx)
+    P = oracle.Problem(n_sub, data.n_items, u_ptr, u_idx, i_ptr, i_idx, prob.d, prob.b,
+                       prob.alpha0, prob.lam, prob.nu)
+    W, H = P.factors(prob.W0[:n_sub], prob.H0)
+    yhat = oracle.predict(P, W, H)
+    state = {"k": 0}
+    nb = prob.d // prob.b
+
+    def step():
+        k = state["k"] % nb
+        oracle.halfstep(P, 0, k, W, H, yhat)
+        oracle.halfstep(P, 1, k, W, H, yhat)
+        state["k"] += 1
+
+    desc = (f"FP64 oracle, one user + one item block step per call on the first {n_sub} users "
+            f"({end} positives) x {data.n_items} items, d={prob.d}, b={prob.b}")
+    return step, n_sub + data.n_items, desc, P.n_threads
+
+
+def cpu_baseline(prob, budget_s=15.0):
+    step, rows, desc, threads = oracle_sample(prob)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        step()
+        n += 1
+        if time.perf_counter() - t0 >= budget_s or n >= 64:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": rows * n / dt, "unit": "rows/s", "cores": threads, "kind": "oracle",
+            "sample": desc + f"; {n} calls in {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return
+    from paper_2110_14044_gb300 import synth
+    prob = synth.preset(WORKLOAD, seed=0)
+    step, rows, desc, threads = oracle_sample(prob)
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = rows * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "rows/s", "cores": threads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    rank, local_rank, world = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    from paper_2110_14044_gb300 import _abi, build, synth
+    build.build()
+    import paper_2110_14044_gb300 as ials
+
+    prob = synth.preset(WORKLOAD, seed=0)
+    data = prob.data
+    prec = _abi.PREC_BF16 if args.precision == "bf16" else _abi.PREC_FP32
+    stream = torch.cuda.current_stream()
+    m = ials.Model(data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu, precision=prec,
+                   graph=not args.no_graph, stream=stream, W0=prob.W0, H0=prob.H0)
+    rows_per_epoch = (data.n_users + data.n_items) * (prob.d // prob.b)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # warm-up
+    for _ in range(args.warmup):
+        m.epoch(1)
+    obj_before = m.objective()
+
+    # timed region: K epochs, device-resident inputs (working set > L2)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    _, st = m.epoch(args.steps)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ms)
+    obj_after = m.objective()
+    ms_per_step = ms / args.steps
+    value = world * rows_per_epoch * args.steps / (ms / 1e3)
+
+    # per-kernel device times over the same number of eager epochs (events per launch)
+    kern, prof_total, _ = _abi.ials_profile_epochs(m.ctx, args.steps)
+    work = _abi.ials_work_model(m.ctx)
+    launches_per_epoch = sum(c for _, c in kern.values()) / args.steps + \
+        kern["gram"][1] / args.steps  # each Gramian mark covers a tile and a reduce kernel
+    dom = max(("sparse", "gram", "rowterm", "residual", "split_solve", "split_resid"),
+              key=lambda k: kern[k][0])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    dms, dcnt = kern[dom]
+    dbytes = work[dom][0] * args.steps  # bytes over all profiled launches
+    achieved = dbytes / (dms / 1e3) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": peak_src,
+                "bytes_per_launch": dbytes / max(dcnt, 1), "ms_per_launch": dms / max(dcnt, 1),
+                "gflops": work[dom][1] * args.steps / (dms / 1e3) / 1e9}
+
+    # end to end through the public API: factors in from pinned host memory,
+    # one epoch, factors back to pinned host memory, every step
+    Wp = torch.from_numpy(prob.W0).pin_memory()
+    Hp = torch.from_numpy(prob.H0).pin_memory()
+    e2e_steps = max(1, min(args.steps, 20))
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        _abi.ials_set_factors(m.ctx, Wp, Hp)
+        _abi.ials_epoch(m.ctx, 1)
+        _abi.ials_get_factors(m.ctx, Wp, Hp)
+    e1.record(stream)
+    barrier()
+    wall = time.perf_counter() - t0
+    e2e_ms = max_over_ranks(max(e0.elapsed_time(e1), wall * 1e3)) / e2e_steps
+    fb = (prob.W0.nbytes + prob.H0.nbytes)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == _abi.PREC_FP32 else "bf16",
+        "data": "synthetic (seeded; no dataset in the container)",
+        "config": {"workload": WORKLOAD_DESC, "precision": args.precision,
+                   "graph": not args.no_graph,
+                   "l2": "inputs larger than L2 (W 70 MB + H 10 MB + residuals 40 MB + CSR 80 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "epoch_s": ms_per_step / 1e3,
+        "rows_per_s_plain": (data.n_users + data.n_items) / (ms_per_step / 1e3),
+        "objective": {"before": obj_before, "after": obj_after, "status": st},
+        "kernels_ms_per_epoch": {k: v[0] / args.steps for k, v in kern.items()},
+        "profiled_epoch_ms": prof_total / args.steps,
+        "roofline": roofline,
+        "e2e": {"value": world * rows_per_epoch / (e2e_ms / 1e3), "unit": "rows/s",
+                "h2d_bytes_per_step": fb, "d2h_bytes_per_step": fb, "ms_per_step": e2e_ms},
+        "gpu_launches": int(round(launches_per_epoch * args.steps)),
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prob)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    m.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

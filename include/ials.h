@@ -1,0 +1,178 @@
+/*
+ * ials.h — C ABI of the GB300 iALS++ library (libials.so).
+ *
+ * iALS++ (Rendle, Krichene, Zhang, Koren, arXiv 2110.14044) learns the
+ * implicit-feedback matrix factorisation yhat(u,i) = <w_u, h_i> (Eq. 1) by
+ * minimising
+ *
+ *   L(W,H) = sum_{(u,i,y,a) in S} a (yhat(u,i) - y)^2
+ *          + alpha0 sum_{u in U} sum_{i in I} yhat(u,i)^2
+ *          + sum_u lambda_u |w_u|^2 + sum_i lambda_i |h_i|^2          (Eq. 2)
+ *
+ * with lambda_r = lambda (1 + nu |S_r|) (nu = 0 gives Eq. 2 as printed), by
+ * subspace coordinate descent: Algorithm 3 visits the coordinate blocks
+ * pi = [k b, (k+1) b) in order and, per block, solves every user's and then
+ * every item's b-dimensional sub-problem exactly with one Newton step
+ * (Eqs. 8-9, sufficient statistics Eqs. 10-12).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an ials_status; nothing throws across the ABI.  On an
+ *    error, ials_last_error() returns a message for the calling thread.
+ *  - Array arguments may be host or device pointers (told apart with
+ *    cudaPointerGetAttributes).  Inputs are copied; the caller keeps ownership
+ *    of its arrays.  The library owns W, H, residuals and all workspaces until
+ *    ials_destroy / ials_foldin_close.
+ *  - Matrices are row-major float32: W is n_users x d, H is n_items x d.
+ *  - All device work of a context runs on the stream given at creation (NULL
+ *    means the legacy default stream).  Calls on one context must not overlap
+ *    (a context is single-threaded); submit/poll on a fold-in server are
+ *    thread-safe.
+ *  - The library runs on the current CUDA device at creation time; it needs an
+ *    sm_103a GPU and fails with IALS_ECUDA otherwise.
+ */
+#ifndef IALS_H
+#define IALS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ials_ctx ials_ctx;
+typedef struct ials_srv ials_srv;
+
+typedef enum {
+    IALS_OK = 0,
+    IALS_EINVAL = 1,     /* bad argument or inconsistent input */
+    IALS_ENOMEM = 2,     /* device or host allocation failed */
+    IALS_ECUDA = 3,      /* a CUDA call failed (message in ials_last_error) */
+    IALS_ENOTPD = 4,     /* some row's Hessian was not positive definite even in FP64 */
+    IALS_EAGAIN = 5,     /* fold-in: not admitted now / result pending */
+    IALS_ETIMEDOUT = 6,  /* fold-in: poll deadline passed */
+    IALS_ENOTFOUND = 7   /* fold-in: unknown ticket */
+} ials_status;
+
+/* Arithmetic of the block step. */
+enum {
+    IALS_PREC_FP32 = 0,  /* FP32 everywhere (FP64 objective, FP64 retry of failed pivots) */
+    IALS_PREC_BF16 = 1   /* BF16 tensor-core Gramian/Hessian products, FP32 accumulate */
+};
+
+/* ials_params.flags */
+enum {
+    IALS_FLAG_GRAPH = 1,      /* capture one epoch as a CUDA graph and replay it */
+    IALS_FLAG_FORCE_FP64 = 2  /* fault injection: treat every FP32 pivot as failed */
+};
+
+typedef struct {
+    int32_t d;          /* embedding dimension; multiple of 4, 4 <= d <= 4096 */
+    int32_t b;          /* block size |pi|; a power of two <= 32 that divides d */
+    double alpha0;      /* weight of the all-pairs term, >= 0 */
+    double lambda;      /* L2 weight, >= 0 */
+    double nu;          /* regularisation scaling: lambda_r = lambda (1 + nu |S_r|), >= 0 */
+    double init_std;    /* W, H drawn N(0, init_std^2) at creation (seeded) */
+    uint64_t seed;
+    int32_t precision;  /* IALS_PREC_* */
+    int32_t flags;      /* IALS_FLAG_* */
+} ials_params;
+
+/* Create a training context (Section 2 problem setting, Algorithm 3 state).
+ *
+ * S is given user-major: u_indptr (n_users + 1, int64, u_indptr[0] = 0,
+ * non-decreasing, u_indptr[n_users] = nnz) and u_items (nnz, int32 item ids in
+ * [0, n_items), no repeats within a row).  i_indptr / i_users may give the
+ * item-major view; if non-NULL it must hold exactly the same pairs (any order
+ * within a row), else IALS_EINVAL.  If NULL the library builds it.
+ * y and alpha are per interaction in user-major order; NULL means all ones
+ * (binary implicit feedback).  alpha must be > 0.
+ * nnz must be < 2^31.  cuda_stream is a cudaStream_t (NULL = default stream).
+ * On success *out receives the context; W and H hold the seeded initial draw. */
+ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_items,
+                        int64_t nnz, const int64_t *u_indptr, const int32_t *u_items,
+                        const int64_t *i_indptr, const int32_t *i_users, const float *y,
+                        const float *alpha, void *cuda_stream, ials_ctx **out);
+
+/* Release every device and host resource of the context (NULL is a no-op). */
+ials_status ials_destroy(ials_ctx *ctx);
+
+/* Run n_epochs epochs of Algorithm 3: recompute the residual cache, then for
+ * each block pi the user pass followed by the item pass.  If objective_after
+ * is non-NULL it receives L(W,H) (FP64) after the last epoch.  Returns
+ * IALS_ENOTPD if some row could not be solved even in FP64 (that row keeps its
+ * old value); the epoch still completes. */
+ials_status ials_epoch(ials_ctx *ctx, int32_t n_epochs, double *objective_after);
+
+/* L(W,H) of Eq. 2 (with lambda_r), accumulated in FP64, from the current W, H. */
+ials_status ials_objective(ials_ctx *ctx, double *out);
+
+/* Copy W (n_users x d) and/or H (n_items x d) out; either pointer may be NULL. */
+ials_status ials_get_factors(ials_ctx *ctx, float *W, float *H);
+
+/* Overwrite W and/or H (either may be NULL); used to resume from a checkpoint
+ * taken at an epoch boundary (Algorithm 3 recomputes the cache per epoch). */
+ials_status ials_set_factors(ials_ctx *ctx, const float *W, const float *H);
+
+/* --- single steps of Algorithm 3 (for step-level checks and profiling) --- */
+
+/* Residual cache e(u,i) = yhat(u,i) - y for all of S ("Compute yhat",
+ * Algorithm 3; Eq. 1).  Stored unweighted, in user-major order. */
+ials_status ials_recompute_residuals(ials_ctx *ctx);
+
+/* One block-side step of Algorithm 3: side 0 updates users (fixed side H),
+ * side 1 updates items (fixed side W); block k covers coordinates
+ * [k b, (k+1) b).  Partial Gramian (Eq. 10), row terms and sparse statistics
+ * (Eqs. 11-12), Newton solve, apply, and in-place residual update. */
+ials_status ials_block_step(ials_ctx *ctx, int32_t side, int32_t block);
+
+/* Copy the residual cache (nnz floats, user-major order) out. */
+ials_status ials_get_residuals(ials_ctx *ctx, float *e);
+
+/* Counters of the last ials_block_step / ials_epoch: rows re-solved in FP64
+ * after a failed FP32 pivot, and rows left unchanged (not positive definite). */
+ials_status ials_last_stats(ials_ctx *ctx, int64_t *n_fp64_retry, int64_t *n_not_pd);
+
+/* Kernel kinds of ials_profile_epochs. */
+enum {
+    IALS_K_RESIDUAL = 0,     /* residual cache recompute */
+    IALS_K_GRAM = 1,         /* partial Gramian (tile + reduce) */
+    IALS_K_ROWTERM = 2,      /* alpha0 x_r G + lambda_r x_{r,pi} */
+    IALS_K_SPARSE = 3,       /* sparse statistics, solve, apply, residual update */
+    IALS_K_SPLIT_SOLVE = 4,  /* long rows: reduce partial statistics and solve */
+    IALS_K_SPLIT_RESID = 5,  /* long rows: residual update */
+    IALS_K_RETRY = 6,        /* FP64 re-solve of failed pivots */
+    IALS_K_OBJECTIVE = 7,
+    IALS_K_COUNT = 8
+};
+
+/* Measurement: run n_epochs epochs without graph capture, with a CUDA event
+ * recorded on the context's stream before and after every kernel launch (or
+ * launch pair, for the Gramian).  kernel_ms[k] and launches[k] (k < n_kinds)
+ * receive the summed device time and the launch count per kind;
+ * *total_ms (if non-NULL) the time from the first to the last event.
+ * Returns like ials_epoch. */
+ials_status ials_profile_epochs(ials_ctx *ctx, int32_t n_epochs, double *kernel_ms,
+                                int64_t *launches, int32_t n_kinds, double *total_ms);
+
+/* Algorithmic work of one epoch per kernel kind, from the context's own work
+ * decomposition: bytes[k] = bytes a kernel of kind k must move (indices,
+ * residuals, gathered b-slices of the fixed side, rows read and written),
+ * flops[k] = floating-point operations counted as in the complexity analysis
+ * (Table 1; symmetric b x b Hessian, b^3/3 Cholesky).  k < n_kinds. */
+ials_status ials_work_model(ials_ctx *ctx, double *bytes, double *flops, int32_t n_kinds);
+
+/* Partial Gramian G = X^T X[:, p0:p0+bs] (Eq. 10) of a row-major n x d float32
+ * device matrix X into the d x bs row-major float32 device array G, on the
+ * given stream, with the library's split-K kernel (precision IALS_PREC_FP32).
+ * Workspace is allocated internally per call.  Synchronous. */
+ials_status ials_partial_gramian(const float *X, int64_t n, int32_t d, int32_t p0, int32_t bs,
+                                 float *G, void *cuda_stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *ials_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IALS_H */

@@ -63,6 +63,8 @@ def _load():
         lib.oracle_halfstep.restype = C.c_int
         lib.oracle_row_step.argtypes = [P, C.c_int, C.c_int, vp, vp, vp, i64, vp]
         lib.oracle_row_step.restype = C.c_int
+        lib.oracle_rows_step.argtypes = [P, C.c_int, C.c_int, vp, vp, vp, vp, i64, vp, vp]
+        lib.oracle_rows_step.restype = C.c_int
         lib.oracle_ialspp.argtypes = [P, C.c_int, vp, vp, vp, vp]
         lib.oracle_ialspp.restype = C.c_int
         lib.oracle_ials.argtypes = [P, C.c_int, vp, vp]
@@ -160,6 +162,22 @@ def row_step(P: Problem, side: int, block: int, W, H, yhat, r: int):
     out = np.empty(bs)
     st = _load().oracle_row_step(P.ref, side, block, _ptr(W), _ptr(H), _ptr(yhat), int(r),
                                  _ptr(out))
+    return st, out
+
+
+def rows_step(P: Problem, side: int, block: int, W, H, yhat, rows):
+    """row_step for many rows at once; returns (status per row, n_rows x bs values)."""
+    W = _c(W, np.float64)
+    H = _c(H, np.float64)
+    yhat = _c(yhat, np.float64)
+    rows = _c(rows, np.int64)
+    bs = min(P.b, P.d - block * P.b)
+    out = np.empty((rows.size, bs))
+    st = np.empty(rows.size, dtype=np.int32)
+    rc = _load().oracle_rows_step(P.ref, side, block, _ptr(W), _ptr(H), _ptr(yhat), _ptr(rows),
+                                  rows.size, _ptr(out), _ptr(st))
+    if rc != OK:
+        raise ValueError("oracle_rows_step failed: %d" % rc)
     return st, out
 
 

@@ -15,6 +15,7 @@
  *   oracle_halfstep        one block pi, one side of Algorithm 3  (Eqs. 10-12)
  *   oracle_ialspp          T epochs of Algorithm 3
  *   oracle_row_step        one row of oracle_halfstep, read-only  (Eqs. 11-12)
+ *   oracle_rows_step       the same for a list of rows
  *   oracle_ials            T epochs of Algorithm 1 (closed form, Eq. 3)
  *   oracle_icd             T epochs of Algorithm 2 (Eqs. 5-7)
  *   oracle_foldin          new-user solve against frozen H (Section 5.1.1
@@ -355,6 +356,27 @@ int oracle_row_step(const oracle_problem *P, int side, int block, const double *
     free(G);
     free(A);
     return st;
+}
+
+/* oracle_row_step for a list of rows (the partial Gramian is formed once).
+ * out_w receives n_sel x bs values; status per row in out_status. */
+int oracle_rows_step(const oracle_problem *P, int side, int block, const double *W,
+                     const double *H, const double *yhat, const int64_t *rows, int64_t n_sel,
+                     double *out_w, int32_t *out_status) {
+    const int d = P->d, b = P->b;
+    if (d <= 0 || b <= 0 || block < 0 || block * b >= d) return ORACLE_EINVAL;
+    const int p0 = block * b, bs = (d - p0 < b) ? d - p0 : b;
+    const double *Fix = side == 0 ? H : W;
+    double *G = malloc(sizeof(double) * d * bs);
+    double *A = malloc(sizeof(double) * (bs * bs + bs));
+    if (!G || !A) { free(G); free(A); return ORACLE_ENOMEM; }
+    partial_gramian(Fix, side == 0 ? P->n_items : P->n_users, d, p0, bs, G);
+    for (int64_t k = 0; k < n_sel; ++k)
+        out_status[k] = row_update(P, side, p0, bs, (double *)(side == 0 ? W : H), Fix, G,
+                                   (double *)yhat, rows[k], A, A + bs * bs, 0, out_w + k * bs);
+    free(G);
+    free(A);
+    return ORACLE_OK;
 }
 
 /* T epochs of Algorithm 3.  If trace is non-NULL it receives the objective

@@ -1,0 +1,136 @@
+// Internal declarations shared by the CUDA translation units of libials.
+// Nothing here is part of the public ABI (see include/ials.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace ials {
+
+// Kernel kinds reported by the profiling entry point (must match include/ials.h).
+enum KernelKind {
+    K_RESIDUAL = 0, K_GRAM = 1, K_ROWTERM = 2, K_SPARSE = 3, K_SPLIT_SOLVE = 4,
+    K_SPLIT_RESID = 5, K_RETRY = 6, K_OBJECTIVE = 7, K_COUNT = 8
+};
+
+// Host-side event marks around kernel launches (measurement only).  mark(k)
+// opens a segment of kind k (k < 0: a gap that is not attributed).
+struct Profiler {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;
+    cudaError_t mark(int k, cudaStream_t s) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        ev.push_back(e);
+        kind.push_back(k);
+        return cudaEventRecord(e, s);
+    }
+    ~Profiler() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
+inline void prof_mark(Profiler *p, int k, cudaStream_t s) {
+    if (p) p->mark(k, s);
+}
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// One unit of sparse work: a whole row, or a chunk of a long ("split") row.
+struct Task {
+    int64_t begin;  // first CSR position
+    int32_t len;    // number of interactions
+    int32_t row;    // row being updated
+    int32_t slot;   // partial-statistics slot for split rows, -1 otherwise
+    int32_t srow;   // index into the split-row table for split rows, -1 otherwise
+};
+
+// A row whose statistics are accumulated by several tasks.
+struct SplitRow {
+    int64_t begin;   // CSR range of the whole row
+    int32_t len;
+    int32_t row;
+    int32_t slot0;   // first partial slot; the row owns [slot0, slot0 + nslots)
+    int32_t nslots;
+};
+
+// Arguments of one block-side step (side = users or items).
+struct StepArgs {
+    // CSR of the side being updated: rows of this side, column ids index the fixed side
+    const int64_t *ptr;
+    const int32_t *idx;
+    const int32_t *pos;     // side 1: CSR position -> user-major residual index; nullptr on side 0
+    float *e;               // residual cache r = yhat - y, user-major order
+    const float *alpha;     // per interaction weights (user-major) or nullptr
+    float *X;               // updated side, n_rows x d
+    const float *F;         // fixed side, n_fixed x d
+    const float *G;         // partial Gramian of F, d x b (row-major)
+    const float *R;         // row terms alpha0 x_r G + lambda_r x_{r,pi}, n_rows x b
+    int32_t n_rows, d, b, p0;
+    float alpha0, lambda, nu;
+    // work decomposition
+    const Task *tasks;
+    int32_t n_tasks;
+    const SplitRow *split;
+    int32_t n_split;
+    const Task *stasks;     // the tasks of split rows (for the residual update)
+    int32_t n_stasks;
+    float *part;            // split partials: slot -> (b*b Hessian, b gradient)
+    float *delta;           // split rows: srow -> delta (b)
+    int32_t *counter;       // work-stealing counter (zeroed before launch)
+    int32_t *retry;         // [0] = count, [1..] = rows to redo in FP64
+    int64_t *stats;         // [0] = FP64 retries, [1] = not positive definite
+    int32_t force_fp64;     // fault injection: every FP32 pivot counts as failed
+    Profiler *prof;         // host only: event marks around launches, or nullptr
+};
+
+// ---------------------------------------------------------------- launchers
+// dense kernels (k_dense.cu)
+cudaError_t launch_residual(const int64_t *u_ptr, const int32_t *u_idx, const float *W,
+                            const float *H, const float *y, int32_t n_users, int32_t d,
+                            float *e, cudaStream_t s);
+// Sum over S of alpha (yhat - y)^2 in FP64, recomputing yhat from W, H.
+// Writes one double per block into part (n_part >= grid) and the total into out.
+cudaError_t launch_sq_loss(const int64_t *u_ptr, const int32_t *u_idx, const float *W,
+                           const float *H, const float *y, const float *alpha,
+                           int32_t n_users, int32_t d, double *part, int32_t n_part,
+                           double *out, cudaStream_t s);
+// sum_r lambda (1 + nu n_r) |x_r|^2 in FP64 -> out (adds to *out if accumulate)
+cudaError_t launch_reg_loss(const int64_t *ptr, const float *X, int32_t n_rows, int32_t d,
+                            double lambda, double nu, double *part, int32_t n_part,
+                            double *out, cudaStream_t s);
+// <A, B>_F of two d x d FP64 matrices -> *out += result
+cudaError_t launch_frobenius(const double *A, const double *B, int32_t n, double alpha0,
+                             double *out, cudaStream_t s);
+
+// Split-K partial Gramian G = X^T X[:, p0:p0+bs] (d x bs).
+// ws must hold gram_ws_floats(n, d, bs) floats.
+int64_t gram_ws_floats(int64_t n, int32_t d, int32_t bs);
+cudaError_t launch_gram(const float *X, int64_t n, int32_t d, int32_t p0, int32_t bs, float *G,
+                        float *ws, cudaStream_t s);
+// Full FP64-accumulated Gramian G64 = X^T X (d x d); ws holds gram64_ws_doubles(n, d).
+int64_t gram64_ws_doubles(int64_t n, int32_t d);
+cudaError_t launch_gram64(const float *X, int64_t n, int32_t d, double *G64, double *ws,
+                          cudaStream_t s);
+// Row terms R[r] = alpha0 * X[r] G + lambda (1 + nu n_r) X[r, p0:p0+bs]  (n_rows x bs)
+cudaError_t launch_rowterm(const float *X, const int64_t *ptr, int32_t n_rows, int32_t d,
+                           int32_t p0, int32_t bs, const float *G, float alpha0, float lambda,
+                           float nu, float *R, cudaStream_t s);
+// N(0, std^2) draws from a counter-based hash (SplitMix64 + Box-Muller)
+cudaError_t launch_init_normal(float *X, int64_t count, double std, uint64_t seed,
+                               uint64_t stream_id, cudaStream_t s);
+
+// sparse kernels (k_sparse_b*.cu): statistics, solve, apply and residual
+// update of one block-side step for block size B (1, 2, 4, 8, 16, 32).
+cudaError_t launch_sparse_b1(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_sparse_b2(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_sparse_b4(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_sparse_b8(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_sparse_b16(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_sparse_b32(const StepArgs &a, cudaStream_t s);
+
+}  // namespace ials

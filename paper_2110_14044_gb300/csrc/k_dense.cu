@@ -1,0 +1,431 @@
+// Dense-side kernels of the iALS++ epoch:
+//   * residual cache e = yhat - y over S (Algorithm 3, "Compute yhat"; Eq. 1)
+//   * FP64 pieces of the objective L(W,H) (Eq. 2)
+//   * split-K partial Gramian G^{pi} = X^T X[:, pi] (Eq. 10) and the full
+//     FP64-accumulated Gramian used by the objective (Eq. 4)
+//   * row terms alpha0 x_r G^{pi} + lambda_r x_{r,pi} (Algorithm 3, gradient
+//     initialisation; first and last terms of Eq. 11)
+//   * seeded normal initialisation of the factors
+#include "ials_internal.cuh"
+
+#include <math.h>
+
+namespace ials {
+
+namespace {
+
+constexpr int kSMs = 152;  // GB300: 2 dies x 76 SMs
+
+__device__ __forceinline__ float dot4(float4 a, float4 b) {
+    return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+}
+
+// ------------------------------------------------------------------ residual
+// One warp per user row.  The warp is split into sub-groups of SG lanes; each
+// sub-group handles one interaction at a time, lane l of the sub-group owning
+// float4 chunks l, l + SG, ... of the d-vector.  MAXV bounds those chunks.
+// LOSS = false: write e[s] = <w_u, h_i> - y_s.
+// LOSS = true : accumulate alpha_s (<w_u, h_i> - y_s)^2 in FP64, one partial per block.
+template <int MAXV, bool LOSS>
+__global__ void __launch_bounds__(256) k_residual(const int64_t *__restrict__ u_ptr,
+                                                  const int32_t *__restrict__ u_idx,
+                                                  const float *__restrict__ W,
+                                                  const float *__restrict__ H,
+                                                  const float *__restrict__ y,
+                                                  const float *__restrict__ alpha,
+                                                  int32_t n_users, int32_t d, int sg_log,
+                                                  float *__restrict__ e, double *__restrict__ part) {
+    const int lane = threadIdx.x & 31;
+    const int SG = 1 << sg_log;
+    const int sub = lane >> sg_log, sl = lane & (SG - 1), nsub = 32 >> sg_log;
+    const int nv4 = d >> 2;
+    const float4 *W4 = reinterpret_cast<const float4 *>(W);
+    const float4 *H4 = reinterpret_cast<const float4 *>(H);
+    const int warps_total = (gridDim.x * blockDim.x) >> 5;
+    double loss = 0.0;
+    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n_users; u += warps_total) {
+        float4 wv[MAXV];
+#pragma unroll
+        for (int m = 0; m < MAXV; ++m) {
+            const int v = sl + m * SG;
+            wv[m] = v < nv4 ? W4[(int64_t)u * nv4 + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const int64_t beg = u_ptr[u], end = u_ptr[u + 1];
+        for (int64_t s0 = beg; s0 < end; s0 += nsub) {
+            const int64_t s = s0 + sub;
+            const bool valid = s < end;
+            float acc = 0.f;
+            if (valid) {
+                const int64_t c = u_idx[s];
+#pragma unroll
+                for (int m = 0; m < MAXV; ++m) {
+                    const int v = sl + m * SG;
+                    if (v < nv4) acc += dot4(wv[m], H4[c * nv4 + v]);
+                }
+            }
+            for (int o = SG >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+            if (valid && sl == 0) {
+                const float r = acc - (y ? y[s] : 1.0f);
+                if (LOSS) {
+                    const double a = alpha ? (double)alpha[s] : 1.0;
+                    loss += a * (double)r * (double)r;
+                } else {
+                    e[s] = r;
+                }
+            }
+        }
+    }
+    if (LOSS) {
+        __shared__ double red[256];
+        red[threadIdx.x] = loss;
+        __syncthreads();
+        for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+    }
+}
+
+// Fixed-order sum of n doubles by one block; *out = (acc ? *out : 0) + scale * sum.
+__global__ void k_sum_parts(const double *__restrict__ part, int32_t n, double scale,
+                            double *out, int acc) {
+    __shared__ double red[256];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) t += part[i];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = (acc ? *out : 0.0) + scale * red[0];
+}
+
+// sum_r lambda (1 + nu n_r) |x_r|^2, one warp per row, FP64 accumulation.
+__global__ void __launch_bounds__(256) k_reg_loss(const int64_t *__restrict__ ptr,
+                                                  const float *__restrict__ X, int32_t n_rows,
+                                                  int32_t d, double lambda, double nu,
+                                                  double *__restrict__ part) {
+    const int lane = threadIdx.x & 31;
+    const int warps_total = (gridDim.x * blockDim.x) >> 5;
+    double acc = 0.0;
+    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_rows; r += warps_total) {
+        double t = 0.0;
+        for (int f = lane; f < d; f += 32) {
+            const double x = X[(int64_t)r * d + f];
+            t += x * x;
+        }
+        acc += lambda * (1.0 + nu * (double)(ptr[r + 1] - ptr[r])) * t;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_frobenius(const double *__restrict__ A, const double *__restrict__ B,
+                            int64_t count, double scale, double *out) {
+    __shared__ double red[256];
+    double t = 0.0;
+    for (int64_t i = threadIdx.x; i < count; i += blockDim.x) t += A[i] * B[i];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out += scale * red[0];
+}
+
+// ------------------------------------------------------------------ Gramian
+// Split-K tile kernel: block (tm, tn, split) accumulates the 64 x 64 output
+// tile [tm*64, +64) x [tn*64, +64) of X^T X[:, p0:p0+bs] over the rows
+// [split*rows_per, +rows_per) of X.  256 threads, 4 x 4 outputs each.
+// F64: accumulate each 16-row slab in FP32 and fold it into FP64 accumulators.
+constexpr int GT = 64, GK = 16;
+
+template <bool F64>
+__global__ void __launch_bounds__(256) k_gram_tile(const float *__restrict__ X, int64_t n,
+                                                   int32_t d, int32_t p0, int32_t bs,
+                                                   int64_t rows_per, void *__restrict__ ws) {
+    __shared__ float As[GK][GT];
+    __shared__ float Bs[GK][GT];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.x * GT, n0 = blockIdx.y * GT;
+    const int64_t k_beg = (int64_t)blockIdx.z * rows_per;
+    const int64_t k_end = min(n, k_beg + rows_per);
+    float acc[4][4];
+    double acc64[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { acc[i][j] = 0.f; acc64[i][j] = 0.0; }
+    for (int64_t k0 = k_beg; k0 < k_end; k0 += GK) {
+        for (int i = tid; i < GK * GT; i += 256) {
+            const int kk = i / GT, mm = i % GT;
+            const int64_t k = k0 + kk;
+            const bool kin = k < k_end;
+            As[kk][mm] = (kin && m0 + mm < d) ? X[k * d + m0 + mm] : 0.f;
+            Bs[kk][mm] = (kin && n0 + mm < bs) ? X[k * d + p0 + n0 + mm] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            const float4 a = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+        }
+        if (F64) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) { acc64[i][j] += (double)acc[i][j]; acc[i][j] = 0.f; }
+        }
+        __syncthreads();
+    }
+    const int64_t base = (int64_t)blockIdx.z * d * bs;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty * 4 + i;
+        if (m >= d) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int nn = n0 + tx * 4 + j;
+            if (nn >= bs) continue;
+            if (F64) static_cast<double *>(ws)[base + (int64_t)m * bs + nn] = acc64[i][j];
+            else static_cast<float *>(ws)[base + (int64_t)m * bs + nn] = acc[i][j];
+        }
+    }
+}
+
+// Fixed-order reduction of the split-K partials.
+template <typename T>
+__global__ void k_gram_reduce(const T *__restrict__ ws, int32_t nsplit, int64_t count,
+                              T *__restrict__ G) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    T t = 0;
+    for (int s = 0; s < nsplit; ++s) t += ws[(int64_t)s * count + i];
+    G[i] = t;
+}
+
+struct GramPlan {
+    int tm, tn, nsplit;
+    int64_t rows_per;
+};
+
+GramPlan gram_plan(int64_t n, int32_t d, int32_t bs) {
+    GramPlan p;
+    p.tm = (d + GT - 1) / GT;
+    p.tn = (bs + GT - 1) / GT;
+    const int64_t tiles = (int64_t)p.tm * p.tn;
+    int64_t ns = (2 * kSMs + tiles - 1) / tiles;
+    const int64_t kblocks = (n + GK - 1) / GK;
+    if (ns > kblocks) ns = kblocks;
+    if (ns < 1) ns = 1;
+    const int64_t per_blocks = (kblocks + ns - 1) / ns;
+    p.rows_per = per_blocks * GK;
+    p.nsplit = (int)((n + p.rows_per - 1) / p.rows_per);
+    if (p.nsplit < 1) p.nsplit = 1;
+    return p;
+}
+
+// ------------------------------------------------------------------ row terms
+// R[r, f] = alpha0 * sum_k X[r, k] G[k, f] + lambda (1 + nu n_r) X[r, p0 + f]
+// 64 x 64 output tile per block, K = d in slabs of 16.
+__global__ void __launch_bounds__(256) k_rowterm(const float *__restrict__ X,
+                                                 const int64_t *__restrict__ ptr, int32_t n_rows,
+                                                 int32_t d, int32_t p0, int32_t bs,
+                                                 const float *__restrict__ G, float alpha0,
+                                                 float lambda, float nu, float *__restrict__ R) {
+    __shared__ float As[GK][GT + 4];
+    __shared__ float Bs[GK][GT];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t r0 = (int64_t)blockIdx.x * GT;
+    const int n0 = blockIdx.y * GT;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < d; k0 += GK) {
+        for (int i = tid; i < GK * GT; i += 256) {
+            const int rr = i / GK, kk = i % GK;
+            const int64_t r = r0 + rr;
+            const int k = k0 + kk;
+            As[kk][rr] = (r < n_rows && k < d) ? X[r * d + k] : 0.f;
+            const int kb = i / GT, nn = i % GT;
+            Bs[kb][nn] = (k0 + kb < d && n0 + nn < bs) ? G[(int64_t)(k0 + kb) * bs + n0 + nn] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            float av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+            bv[0] = b.x; bv[1] = b.y; bv[2] = b.z; bv[3] = b.w;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t r = r0 + ty * 4 + i;
+        if (r >= n_rows) continue;
+        const float lam = lambda * (1.0f + nu * (float)(ptr[r + 1] - ptr[r]));
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int f = n0 + tx * 4 + j;
+            if (f >= bs) continue;
+            R[r * bs + f] = alpha0 * acc[i][j] + lam * X[r * d + p0 + f];
+        }
+    }
+}
+
+// ------------------------------------------------------------------- init
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__global__ void k_init_normal(float *X, int64_t count, double std, uint64_t key) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const uint64_t a = splitmix64(key ^ (2 * (uint64_t)i));
+    const uint64_t b = splitmix64(key ^ (2 * (uint64_t)i + 1));
+    const double u1 = ((double)(a >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    const double u2 = ((double)(b >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    X[i] = (float)(std * sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));
+}
+
+int residual_grid(int32_t n_rows) {
+    int g = (n_rows + 7) / 8;
+    return g < 4 * kSMs ? (g > 0 ? g : 1) : 4 * kSMs;
+}
+
+template <bool LOSS>
+cudaError_t launch_residual_impl(const int64_t *u_ptr, const int32_t *u_idx, const float *W,
+                                 const float *H, const float *y, const float *alpha,
+                                 int32_t n_users, int32_t d, float *e, double *part,
+                                 int grid, cudaStream_t s) {
+    const int nv4 = d / 4;
+    int sg_log = 0;
+    while ((2 << sg_log) <= nv4 && (2 << sg_log) <= 32) ++sg_log;
+    const int SG = 1 << sg_log;
+    const int maxv = (nv4 + SG - 1) / SG;
+#define IALS_RES(MV)                                                                         \
+    k_residual<MV, LOSS><<<grid, 256, 0, s>>>(u_ptr, u_idx, W, H, y, alpha, n_users, d,      \
+                                              sg_log, e, part)
+    if (maxv <= 1) IALS_RES(1);
+    else if (maxv <= 2) IALS_RES(2);
+    else if (maxv <= 4) IALS_RES(4);
+    else if (maxv <= 8) IALS_RES(8);
+    else if (maxv <= 16) IALS_RES(16);
+    else if (maxv <= 32) IALS_RES(32);
+    else return cudaErrorInvalidValue;
+#undef IALS_RES
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_residual(const int64_t *u_ptr, const int32_t *u_idx, const float *W,
+                            const float *H, const float *y, int32_t n_users, int32_t d,
+                            float *e, cudaStream_t s) {
+    if (n_users == 0) return cudaSuccess;
+    return launch_residual_impl<false>(u_ptr, u_idx, W, H, y, nullptr, n_users, d, e, nullptr,
+                                       residual_grid(n_users), s);
+}
+
+cudaError_t launch_sq_loss(const int64_t *u_ptr, const int32_t *u_idx, const float *W,
+                           const float *H, const float *y, const float *alpha,
+                           int32_t n_users, int32_t d, double *part, int32_t n_part,
+                           double *out, cudaStream_t s) {
+    int grid = residual_grid(n_users);
+    if (grid > n_part) grid = n_part;
+    cudaError_t err = launch_residual_impl<true>(u_ptr, u_idx, W, H, y, alpha, n_users, d,
+                                                 nullptr, part, grid, s);
+    if (err != cudaSuccess) return err;
+    k_sum_parts<<<1, 256, 0, s>>>(part, grid, 1.0, out, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reg_loss(const int64_t *ptr, const float *X, int32_t n_rows, int32_t d,
+                            double lambda, double nu, double *part, int32_t n_part, double *out,
+                            cudaStream_t s) {
+    int grid = residual_grid(n_rows);
+    if (grid > n_part) grid = n_part;
+    k_reg_loss<<<grid, 256, 0, s>>>(ptr, X, n_rows, d, lambda, nu, part);
+    k_sum_parts<<<1, 256, 0, s>>>(part, grid, 1.0, out, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_frobenius(const double *A, const double *B, int32_t n, double alpha0,
+                             double *out, cudaStream_t s) {
+    k_frobenius<<<1, 256, 0, s>>>(A, B, (int64_t)n * n, alpha0, out);
+    return cudaGetLastError();
+}
+
+int64_t gram_ws_floats(int64_t n, int32_t d, int32_t bs) {
+    GramPlan p = gram_plan(n, d, bs);
+    return (int64_t)p.nsplit * d * bs;
+}
+
+cudaError_t launch_gram(const float *X, int64_t n, int32_t d, int32_t p0, int32_t bs, float *G,
+                        float *ws, cudaStream_t s) {
+    const int64_t count = (int64_t)d * bs;
+    if (n == 0) return cudaMemsetAsync(G, 0, sizeof(float) * count, s);
+    GramPlan p = gram_plan(n, d, bs);
+    k_gram_tile<false><<<dim3(p.tm, p.tn, p.nsplit), 256, 0, s>>>(X, n, d, p0, bs, p.rows_per, ws);
+    k_gram_reduce<float><<<(unsigned)((count + 255) / 256), 256, 0, s>>>(ws, p.nsplit, count, G);
+    return cudaGetLastError();
+}
+
+int64_t gram64_ws_doubles(int64_t n, int32_t d) {
+    GramPlan p = gram_plan(n, d, d);
+    return (int64_t)p.nsplit * d * d;
+}
+
+cudaError_t launch_gram64(const float *X, int64_t n, int32_t d, double *G64, double *ws,
+                          cudaStream_t s) {
+    const int64_t count = (int64_t)d * d;
+    if (n == 0) return cudaMemsetAsync(G64, 0, sizeof(double) * count, s);
+    GramPlan p = gram_plan(n, d, d);
+    k_gram_tile<true><<<dim3(p.tm, p.tn, p.nsplit), 256, 0, s>>>(X, n, d, 0, d, p.rows_per, ws);
+    k_gram_reduce<double><<<(unsigned)((count + 255) / 256), 256, 0, s>>>(ws, p.nsplit, count, G64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowterm(const float *X, const int64_t *ptr, int32_t n_rows, int32_t d,
+                           int32_t p0, int32_t bs, const float *G, float alpha0, float lambda,
+                           float nu, float *R, cudaStream_t s) {
+    if (n_rows == 0) return cudaSuccess;
+    dim3 grid((n_rows + GT - 1) / GT, (bs + GT - 1) / GT);
+    k_rowterm<<<grid, 256, 0, s>>>(X, ptr, n_rows, d, p0, bs, G, alpha0, lambda, nu, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_normal(float *X, int64_t count, double std, uint64_t seed,
+                               uint64_t stream_id, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    const uint64_t key = seed * 0x9E3779B97F4A7C15ull + stream_id * 0xD1B54A32D192ED03ull + 1;
+    k_init_normal<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(X, count, std, key);
+    return cudaGetLastError();
+}
+
+}  // namespace ials

@@ -1,0 +1,8 @@
+// Block size 16 instantiation of the sparse block step (see k_sparse_impl.cuh).
+#include "k_sparse_impl.cuh"
+
+namespace ials {
+cudaError_t launch_sparse_b16(const StepArgs &a, cudaStream_t s) {
+    return launch_sparse_dispatch<16>(a, s);
+}
+}  // namespace ials

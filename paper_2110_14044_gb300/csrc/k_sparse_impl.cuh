@@ -1,0 +1,527 @@
+// Sparse block step of Algorithm 3 for block sizes B <= 32 (one warp per task).
+//
+// For a row r of the side being updated (fixed side F, block pi = [p0, p0+B)):
+//   g_r  = R_r + sum_{s in S_r} alpha_s e_s f_{c_s, pi}                 (Eq. 11)
+//   A_r  = sum_{s in S_r} alpha_s f_{c_s,pi} f_{c_s,pi}^T
+//          + alpha0 G_pipi + lambda_r I                                 (Eq. 12)
+//   delta = A_r^{-1} g_r ;  x_{r,pi} -= delta ;  e_s -= <delta, f_{c_s,pi}>  (Eq. 9, Eq. 7 generalised)
+// where R_r = alpha0 x_r G^{pi} + lambda_r x_{r,pi} comes from the row-term kernel
+// and e = yhat - y is the residual cache in user-major order (items reach it
+// through the CSR-position map `pos`).
+//
+// Warp layout: lane l owns column col = l % B of A_r (and entry col of g_r);
+// the 32 / B sub-groups of B lanes accumulate interleaved interactions and
+// are summed by a fixed xor butterfly at the end, so results do not depend on
+// scheduling.  Interactions are staged 32 at a time: their fixed-side slices
+// f_{c,pi} are gathered with 16-byte loads into a padded shared-memory tile
+// (row stride B + 4 floats) and then read back as broadcasts.
+//
+// Long rows are cut into several tasks that write partial (A, g) to a slot;
+// k_split_solve sums the slots of a row in slot order and solves it, and
+// k_split_resid applies its residual update.  A row whose FP32 Cholesky meets
+// a non-positive (or collapsed) pivot is queued; k_retry re-solves it in FP64
+// from scratch.
+#pragma once
+
+#include "ials_internal.cuh"
+
+namespace ials {
+
+template <int B>
+struct SparseCfg {
+    static constexpr int G = 32 / B;               // sub-groups per warp
+    static constexpr int SB = B < 4 ? 4 : B + 4;   // shared row stride (floats)
+    static constexpr int CH = 32;                  // interactions staged per chunk
+    static constexpr int VPAD = (B + 3) / 4 * 4;
+    static constexpr int LSTR = B + 1;             // stride of the L factor copy
+    static constexpr int WARP_FLOATS_RAW = CH * SB + 3 * CH + VPAD + B * LSTR;
+    static constexpr int WARP_FLOATS = (WARP_FLOATS_RAW + 3) / 4 * 4;
+    static constexpr int GPP_FLOATS = (B * B + 3) / 4 * 4;
+    static constexpr int WARPS = 8;
+    static constexpr int SMEM_BYTES = (GPP_FLOATS + WARPS * WARP_FLOATS) * 4;
+};
+
+struct WarpSmem {
+    float *h;    // CH x SB fixed-side slices
+    float *e;    // CH (alpha * e when weighted)
+    float *a;    // CH alpha
+    int *c;      // CH column ids
+    float *v;    // VPAD vector buffer (Cholesky column, delta)
+    float *L;    // B x (B+1) copy of the Cholesky factor
+};
+
+template <int B>
+__device__ __forceinline__ WarpSmem warp_smem(float *base, int warp) {
+    using C = SparseCfg<B>;
+    WarpSmem w;
+    float *p = base + C::GPP_FLOATS + warp * C::WARP_FLOATS;
+    w.h = p;
+    w.e = w.h + C::CH * C::SB;
+    w.a = w.e + C::CH;
+    w.c = reinterpret_cast<int *>(w.a + C::CH);
+    w.v = reinterpret_cast<float *>(w.c + C::CH);
+    w.L = w.v + C::VPAD;
+    return w;
+}
+
+// Stage `cnt` (<= 32) interactions starting at CSR position `begin`: column
+// ids, residual (weighted) and the gathered slices.  Lane k keeps the residual
+// index of interaction k in q.  LOAD_E = false skips residual / weight loads.
+template <int B, bool PERM, bool HAS_A, bool LOAD_E>
+__device__ __forceinline__ void stage_chunk(const StepArgs &a, int64_t begin, int cnt, int lane,
+                                            const WarpSmem &w, int64_t &q) {
+    using C = SparseCfg<B>;
+    __syncwarp();
+    if (lane < cnt) {
+        const int64_t s = begin + lane;
+        w.c[lane] = a.idx[s];
+        q = PERM ? (int64_t)a.pos[s] : s;
+        if (LOAD_E) {
+            const float r = a.e[q];
+            if (HAS_A) {
+                const float al = a.alpha[q];
+                w.e[lane] = al * r;
+                w.a[lane] = al;
+            } else {
+                w.e[lane] = r;
+            }
+        }
+    }
+    __syncwarp();
+    if constexpr (B >= 4) {
+        constexpr int VPR = B / 4;        // float4 per slice
+        constexpr int RPP = 32 / VPR;     // slices per pass
+        constexpr int NP = C::CH / RPP;   // passes
+        const int v = lane % VPR, rr = lane / VPR;
+        float4 t[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const int k = p * RPP + rr;
+            if (k < cnt) {
+                const float4 *src = reinterpret_cast<const float4 *>(
+                    a.F + (int64_t)w.c[k] * a.d + a.p0);
+                t[p] = __ldg(src + v);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const int k = p * RPP + rr;
+            if (k < cnt) reinterpret_cast<float4 *>(w.h + k * C::SB)[v] = t[p];
+        }
+    } else {
+        if (lane < cnt) {
+            const float *src = a.F + (int64_t)w.c[lane] * a.d + a.p0;
+#pragma unroll
+            for (int j = 0; j < B; ++j) w.h[lane * C::SB + j] = __ldg(src + j);
+        }
+    }
+    __syncwarp();
+}
+
+// Warp Cholesky solve A delta = g.  Lane l holds row/column col = l % B of the
+// symmetric matrix in A[] and entry col of g.  Returns false (warp-uniform) if
+// a pivot is not positive, not finite, or has lost all but ~17 bits relative to
+// the original diagonal.  On success `delta` holds entry col of the solution.
+template <int B>
+__device__ __forceinline__ bool chol_solve(float (&A)[B], float g, int col, int sub,
+                                           const WarpSmem &w, bool force_fail, float &delta) {
+    float diag0 = 0.f;
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+        if (j == col) diag0 = A[j];
+    bool ok = !force_fail;
+    float inv_diag = 0.f;
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+        const float akk = __shfl_sync(kFull, A[k], k);
+        const float d0 = __shfl_sync(kFull, diag0, k);
+        ok = ok && (akk > 1e-5f * d0) && (akk <= 3.0e38f);
+        const float lkk = sqrtf(fmaxf(akk, 1e-30f));
+        const float inv = 1.0f / lkk;
+        const float lck = A[k] * inv;
+        if (col == k) inv_diag = inv;
+        A[k] = lck;
+        __syncwarp();
+        if (sub == 0) w.v[col] = lck;
+        __syncwarp();
+#pragma unroll
+        for (int j = k + 1; j < B; ++j) A[j] -= lck * w.v[j];
+    }
+    if (!ok) return false;
+    // forward: L z = g
+    float z = g;
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+        const float zk = __shfl_sync(kFull, z * inv_diag, k);
+        if (col > k) z -= A[k] * zk;
+        else if (col == k) z = zk;
+    }
+    // backward: L^T x = z, with the rows of L copied to shared memory
+    __syncwarp();
+    if (sub == 0) {
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+            if (j <= col) w.L[col * SparseCfg<B>::LSTR + j] = A[j];
+    }
+    __syncwarp();
+    float x = z;
+#pragma unroll
+    for (int k = B - 1; k >= 0; --k) {
+        const float xk = __shfl_sync(kFull, x * inv_diag, k);
+        if (col < k) x -= w.L[k * SparseCfg<B>::LSTR + col] * xk;
+        else if (col == k) x = xk;
+    }
+    delta = x;
+    return isfinite(x);
+}
+
+template <int B>
+__device__ __forceinline__ float dot_slice(const float *v, const float *h) {
+    float t = 0.f;
+    if constexpr (B >= 4) {
+#pragma unroll
+        for (int j = 0; j < B; j += 4) {
+            const float4 a = *reinterpret_cast<const float4 *>(v + j);
+            const float4 b = *reinterpret_cast<const float4 *>(h + j);
+            t += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < B; ++j) t += v[j] * h[j];
+    }
+    return t;
+}
+
+__device__ __forceinline__ void queue_retry(const StepArgs &a, int lane, int row) {
+    if (lane == 0) {
+        const int i = atomicAdd(a.retry, 1);
+        a.retry[1 + i] = row;
+    }
+}
+
+// ------------------------------------------------------------- main kernel
+template <int B, bool PERM, bool HAS_A>
+__global__ void __launch_bounds__(256, 2) k_sparse(const StepArgs a) {
+    using C = SparseCfg<B>;
+    extern __shared__ float4 smem4[];
+    float *smem = reinterpret_cast<float *>(smem4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *sGpp = smem;
+    for (int i = threadIdx.x; i < B * B; i += blockDim.x)
+        sGpp[i] = a.alpha0 * a.G[(int64_t)(a.p0 + i / B) * B + (i % B)];
+    __syncthreads();
+    const WarpSmem w = warp_smem<B>(smem, warp);
+    const int col = lane % B, sub = lane / B;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(a.counter, 1);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= a.n_tasks) break;
+        const Task tk = a.tasks[t];
+        float acc[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) acc[j] = 0.f;
+        float g = 0.f;
+        int64_t q = 0;
+        for (int c0 = 0; c0 < tk.len; c0 += C::CH) {
+            const int cnt = min(C::CH, tk.len - c0);
+            stage_chunk<B, PERM, HAS_A, true>(a, tk.begin + c0, cnt, lane, w, q);
+            for (int k = sub; k < cnt; k += C::G) {
+                const float *hk = w.h + k * C::SB;
+                const float hc = hk[col];
+                g += w.e[k] * hc;
+                const float hw = HAS_A ? hc * w.a[k] : hc;
+                if constexpr (B >= 4) {
+#pragma unroll
+                    for (int j = 0; j < B; j += 4) {
+                        const float4 v = *reinterpret_cast<const float4 *>(hk + j);
+                        acc[j] += v.x * hw;
+                        acc[j + 1] += v.y * hw;
+                        acc[j + 2] += v.z * hw;
+                        acc[j + 3] += v.w * hw;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < B; ++j) acc[j] += hk[j] * hw;
+                }
+            }
+        }
+#pragma unroll
+        for (int m = B; m < 32; m <<= 1) {
+#pragma unroll
+            for (int j = 0; j < B; ++j) acc[j] += __shfl_xor_sync(kFull, acc[j], m);
+            g += __shfl_xor_sync(kFull, g, m);
+        }
+        if (tk.slot >= 0) {  // a chunk of a long row: store the partial statistics
+            if (sub == 0) {
+                float *P = a.part + (int64_t)tk.slot * (B * B + B);
+#pragma unroll
+                for (int j = 0; j < B; ++j) P[j * B + col] = acc[j];
+                P[B * B + col] = g;
+            }
+            continue;
+        }
+        const int row = tk.row;
+        const float lam = a.lambda * (1.0f + a.nu * (float)tk.len);
+#pragma unroll
+        for (int j = 0; j < B; ++j) acc[j] += sGpp[j * B + col] + (j == col ? lam : 0.f);
+        g += a.R[(int64_t)row * B + col];
+        float delta;
+        if (!chol_solve<B>(acc, g, col, sub, w, a.force_fp64 != 0, delta)) {
+            queue_retry(a, lane, row);
+            continue;
+        }
+        if (sub == 0) a.X[(int64_t)row * a.d + a.p0 + col] -= delta;
+        __syncwarp();
+        if (sub == 0) w.v[col] = delta;
+        __syncwarp();
+        if (tk.len <= C::CH) {  // the slices are still staged
+            if (lane < tk.len) a.e[q] -= dot_slice<B>(w.v, w.h + lane * C::SB);
+        } else {
+            for (int c0 = 0; c0 < tk.len; c0 += C::CH) {
+                const int cnt = min(C::CH, tk.len - c0);
+                stage_chunk<B, PERM, HAS_A, false>(a, tk.begin + c0, cnt, lane, w, q);
+                if (lane < cnt) a.e[q] -= dot_slice<B>(w.v, w.h + lane * C::SB);
+            }
+        }
+    }
+}
+
+// One warp per split row: sum the partial slots in order, add the dense terms, solve, apply.
+template <int B>
+__global__ void __launch_bounds__(256) k_split_solve(const StepArgs a) {
+    using C = SparseCfg<B>;
+    extern __shared__ float4 smem4[];
+    float *smem = reinterpret_cast<float *>(smem4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const WarpSmem w = warp_smem<B>(smem, warp);
+    const int col = lane % B, sub = lane / B;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < a.n_split; i += nw) {
+        const SplitRow sr = a.split[i];
+        float acc[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) acc[j] = 0.f;
+        float g = 0.f;
+        for (int sl = 0; sl < sr.nslots; ++sl) {
+            const float *P = a.part + (int64_t)(sr.slot0 + sl) * (B * B + B);
+#pragma unroll
+            for (int j = 0; j < B; ++j) acc[j] += P[j * B + col];
+            g += P[B * B + col];
+        }
+        const float lam = a.lambda * (1.0f + a.nu * (float)sr.len);
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+            acc[j] += a.alpha0 * a.G[(int64_t)(a.p0 + j) * B + col] + (j == col ? lam : 0.f);
+        g += a.R[(int64_t)sr.row * B + col];
+        float delta = 0.f;
+        const bool ok = chol_solve<B>(acc, g, col, sub, w, a.force_fp64 != 0, delta);
+        if (!ok) {
+            queue_retry(a, lane, sr.row);
+            delta = 0.f;  // k_split_resid leaves the row's residuals alone
+        } else if (sub == 0) {
+            a.X[(int64_t)sr.row * a.d + a.p0 + col] -= delta;
+        }
+        if (sub == 0) a.delta[(int64_t)i * B + col] = delta;
+    }
+}
+
+// One warp per chunk of a split row: e_s -= <delta_row, f_{c_s,pi}>.
+template <int B, bool PERM>
+__global__ void __launch_bounds__(256) k_split_resid(const StepArgs a, const Task *__restrict__ stasks,
+                                                     int32_t n_stasks) {
+    using C = SparseCfg<B>;
+    extern __shared__ float4 smem4[];
+    float *smem = reinterpret_cast<float *>(smem4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const WarpSmem w = warp_smem<B>(smem, warp);
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_stasks; t += nw) {
+        const Task tk = stasks[t];
+        __syncwarp();
+        if (lane < B) w.v[lane] = a.delta[(int64_t)tk.srow * B + lane];
+        int64_t q = 0;
+        for (int c0 = 0; c0 < tk.len; c0 += C::CH) {
+            const int cnt = min(C::CH, tk.len - c0);
+            stage_chunk<B, PERM, false, false>(a, tk.begin + c0, cnt, lane, w, q);
+            if (lane < cnt) a.e[q] -= dot_slice<B>(w.v, w.h + lane * C::SB);
+        }
+    }
+}
+
+// FP64 re-solve of queued rows: statistics accumulated from scratch in FP64
+// (the FP32 row term R_r is reused), Cholesky in FP64.  A row that still has
+// a pivot that is not positive, or below 1e-13 of its original diagonal (the
+// matrix is singular to FP64 working accuracy), is counted as not positive
+// definite and left unchanged.
+template <int B, bool PERM, bool HAS_A>
+__global__ void __launch_bounds__(128) k_retry(const StepArgs a) {
+    __shared__ double sv[4][32];
+    __shared__ double sL[4][B * (B + 1)];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int col = lane % B, sub = lane / B;
+    constexpr int G = 32 / B;
+    const int count = *(volatile int *)a.retry;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < count; i += nw) {
+        const int row = a.retry[1 + i];
+        const int64_t beg = a.ptr[row], end = a.ptr[row + 1];
+        double A[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) A[j] = 0.0;
+        double g = 0.0;
+        for (int64_t s = beg + sub; s < end; s += G) {
+            const int64_t q = PERM ? (int64_t)a.pos[s] : s;
+            const float *h = a.F + (int64_t)a.idx[s] * a.d + a.p0;
+            const double al = HAS_A ? (double)a.alpha[q] : 1.0;
+            const double hc = h[col];
+            g += al * (double)a.e[q] * hc;
+#pragma unroll
+            for (int j = 0; j < B; ++j) A[j] += al * (double)h[j] * hc;
+        }
+#pragma unroll
+        for (int m = B; m < 32; m <<= 1) {
+#pragma unroll
+            for (int j = 0; j < B; ++j) A[j] += __shfl_xor_sync(kFull, A[j], m);
+            g += __shfl_xor_sync(kFull, g, m);
+        }
+        const double lam = (double)a.lambda * (1.0 + (double)a.nu * (double)(end - beg));
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+            A[j] += (double)a.alpha0 * (double)a.G[(int64_t)(a.p0 + j) * B + col] +
+                    (j == col ? lam : 0.0);
+        g += (double)a.R[(int64_t)row * B + col];
+        // right-looking Cholesky, lane col holds row col
+        double diag0 = 0.0;
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+            if (j == col) diag0 = A[j];
+        bool ok = true;
+        double inv_diag = 0.0;
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const double akk = __shfl_sync(kFull, A[k], k);
+            const double d0 = __shfl_sync(kFull, diag0, k);
+            ok = ok && (akk > 1e-13 * d0) && (akk < 1e300);
+            const double lkk = sqrt(akk > 0.0 ? akk : 1e-300);
+            const double lck = A[k] / lkk;
+            if (col == k) inv_diag = 1.0 / lkk;
+            A[k] = lck;
+            __syncwarp();
+            if (sub == 0) sv[warp][col] = lck;
+            __syncwarp();
+#pragma unroll
+            for (int j = k + 1; j < B; ++j) A[j] -= lck * sv[warp][j];
+        }
+        if (!ok) {
+            if (lane == 0) atomicAdd((unsigned long long *)&a.stats[1], 1ull);
+            continue;
+        }
+        double z = g;
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const double zk = __shfl_sync(kFull, z * inv_diag, k);
+            if (col > k) z -= A[k] * zk;
+            else if (col == k) z = zk;
+        }
+        __syncwarp();
+        if (sub == 0) {
+#pragma unroll
+            for (int j = 0; j < B; ++j)
+                if (j <= col) sL[warp][col * (B + 1) + j] = A[j];
+        }
+        __syncwarp();
+        double x = z;
+#pragma unroll
+        for (int k = B - 1; k >= 0; --k) {
+            const double xk = __shfl_sync(kFull, x * inv_diag, k);
+            if (col < k) x -= sL[warp][k * (B + 1) + col] * xk;
+            else if (col == k) x = xk;
+        }
+        const float delta = (float)x;
+        if (sub == 0) a.X[(int64_t)row * a.d + a.p0 + col] -= delta;
+        __syncwarp();
+        if (sub == 0) sv[warp][col] = (double)delta;
+        __syncwarp();
+        for (int64_t s = beg + lane; s < end; s += 32) {
+            const int64_t q = PERM ? (int64_t)a.pos[s] : s;
+            const float *h = a.F + (int64_t)a.idx[s] * a.d + a.p0;
+            float t = 0.f;
+#pragma unroll
+            for (int j = 0; j < B; ++j) t += (float)sv[warp][j] * h[j];
+            a.e[q] -= t;
+        }
+        if (lane == 0) atomicAdd((unsigned long long *)&a.stats[0], 1ull);
+    }
+}
+
+template <int B, bool PERM, bool HAS_A>
+cudaError_t launch_step_b(const StepArgs &a, cudaStream_t s) {
+    using C = SparseCfg<B>;
+    static bool attr_done = false;
+    static int per_sm = 0;
+    if (!attr_done) {
+        cudaError_t e1 = cudaFuncSetAttribute(k_sparse<B, PERM, HAS_A>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+        cudaError_t e2 = cudaFuncSetAttribute(k_split_solve<B>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+        cudaError_t e3 = cudaFuncSetAttribute(k_split_resid<B, PERM>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+        if (e1 != cudaSuccess) return e1;
+        if (e2 != cudaSuccess) return e2;
+        if (e3 != cudaSuccess) return e3;
+        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_sparse<B, PERM, HAS_A>, C::WARPS * 32, C::SMEM_BYTES);
+        if (err != cudaSuccess) return err;
+        if (per_sm < 1) per_sm = 1;
+        attr_done = true;
+    }
+    int grid = 152 * per_sm;
+    const int need = (a.n_tasks + C::WARPS - 1) / C::WARPS;
+    if (grid > need) grid = need > 0 ? need : 1;
+    if (a.n_tasks > 0) {
+        prof_mark(a.prof, K_SPARSE, s);
+        k_sparse<B, PERM, HAS_A><<<grid, C::WARPS * 32, C::SMEM_BYTES, s>>>(a);
+        prof_mark(a.prof, -1, s);
+    }
+    if (a.n_split > 0) {
+        const int g2 = (a.n_split + C::WARPS - 1) / C::WARPS;
+        prof_mark(a.prof, K_SPLIT_SOLVE, s);
+        k_split_solve<B><<<g2, C::WARPS * 32, C::SMEM_BYTES, s>>>(a);
+        prof_mark(a.prof, -1, s);
+    }
+    return cudaGetLastError();
+}
+
+template <int B, bool PERM, bool HAS_A>
+cudaError_t launch_split_resid_b(const StepArgs &a, cudaStream_t s) {
+    using C = SparseCfg<B>;
+    if (a.n_stasks > 0) {
+        int g3 = (a.n_stasks + C::WARPS - 1) / C::WARPS;
+        if (g3 > 152 * 4) g3 = 152 * 4;
+        prof_mark(a.prof, K_SPLIT_RESID, s);
+        k_split_resid<B, PERM><<<g3, C::WARPS * 32, C::SMEM_BYTES, s>>>(a, a.stasks, a.n_stasks);
+        prof_mark(a.prof, -1, s);
+    }
+    prof_mark(a.prof, K_RETRY, s);
+    k_retry<B, PERM, HAS_A><<<38, 128, 0, s>>>(a);
+    prof_mark(a.prof, -1, s);
+    return cudaGetLastError();
+}
+
+// Whole sparse part of a block-side step for block size B.
+template <int B, bool PERM, bool HAS_A>
+cudaError_t launch_sparse_all(const StepArgs &a, cudaStream_t s) {
+    cudaError_t e = launch_step_b<B, PERM, HAS_A>(a, s);
+    if (e != cudaSuccess) return e;
+    return launch_split_resid_b<B, PERM, HAS_A>(a, s);
+}
+
+template <int B>
+cudaError_t launch_sparse_dispatch(const StepArgs &a, cudaStream_t s) {
+    const bool perm = a.pos != nullptr, wa = a.alpha != nullptr;
+    if (perm) return wa ? launch_sparse_all<B, true, true>(a, s) : launch_sparse_all<B, true, false>(a, s);
+    return wa ? launch_sparse_all<B, false, true>(a, s) : launch_sparse_all<B, false, false>(a, s);
+}
+
+}  // namespace ials

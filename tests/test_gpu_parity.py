@@ -1,0 +1,328 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: the plain FP32 path must match the oracle to 1e-5 relative
+objective per epoch and 1e-3 maximum relative embedding error, where the
+relative error of a row is |x_r - x*_r| / max(|x*_r|, 1e-6 median_r |x*_r|).
+Single block-side steps are held to 1e-4 (a handful of FP32 roundings).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_14044_gb300 import _abi, synth
+
+pytestmark = pytest.mark.gpu
+
+OBJ_TOL = 1e-5
+EMB_TOL = 1e-3
+STEP_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_14044_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def Model(*a, **k):
+    import paper_2110_14044_gb300 as ials
+    return ials.Model(*a, **k)
+
+
+def rel_embed_err(X, Xref):
+    X = np.asarray(X, np.float64)
+    Xref = np.asarray(Xref, np.float64)
+    nref = np.linalg.norm(Xref, axis=1)
+    floor = max(1e-6 * np.median(nref), 1e-30)
+    return float(np.max(np.linalg.norm(X - Xref, axis=1) / np.maximum(nref, floor)))
+
+
+def small(n_users=300, n_items=200, nnz=6000, seed=0, d=32, len_max=200):
+    prob = synth.preset("parity_2k", seed=seed, n_users=n_users, n_items=n_items, nnz=nnz,
+                        len_max=len_max, d=d)
+    return prob
+
+
+def weights(nnz, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.uniform(0.5, 2.0, nnz).astype(np.float32),
+            rng.uniform(0.5, 3.0, nnz).astype(np.float32))
+
+
+# --------------------------------------------------------- full parity workload
+
+def test_parity_workload_five_epochs():
+    """2,000 x 1,000, 50k positives, d=16, b=8, alpha0=0.1, lambda=1e-3, 5 epochs."""
+    prob = synth.preset("parity_2k", seed=0)
+    data = prob.data
+    m = Model(data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu, W0=prob.W0, H0=prob.H0)
+    objs = []
+    for _ in range(prob.epochs):
+        o, st = m.epoch(1, objective=True)
+        assert st == 0
+        objs.append(o)
+    W, H = m.factors()
+    P = oracle.Problem.from_data(data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu)
+    Wr, Hr, _, trace, st = oracle.ialspp(P, prob.epochs, prob.W0, prob.H0, trace=True)
+    assert st == 0
+    per_epoch = trace.reshape(prob.epochs, -1)[:, -1]
+    rel = np.abs(np.array(objs) - per_epoch) / np.abs(per_epoch)
+    assert rel.max() <= OBJ_TOL, rel
+    assert rel_embed_err(W, Wr) <= EMB_TOL
+    assert rel_embed_err(H, Hr) <= EMB_TOL
+
+
+# --------------------------------------------------------- step-level parity
+
+@pytest.mark.parametrize("b", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_block_steps_match_oracle(b, weighted):
+    d = 32
+    prob = small(d=d, seed=b)
+    data = prob.data
+    y, a = weights(data.nnz, b) if weighted else (None, None)
+    nu = 0.5 if weighted else 0.0
+    m = Model(data, d, b, 0.1, 2e-3, nu, W0=prob.W0, H0=prob.H0, y=y, alpha=a)
+    P = oracle.Problem.from_data(data, d, b, 0.1, 2e-3, nu, y=y, alpha=a)
+    W, H = P.factors(prob.W0, prob.H0)
+    yhat = oracle.predict(P, W, H)
+    m.recompute_residuals()
+    yref = 1.0 if y is None else y.astype(np.float64)
+    np.testing.assert_allclose(m.residuals(), yhat - yref, rtol=1e-5, atol=1e-6)
+    nb = d // b
+    for k in range(min(nb, 3)):
+        for side in (0, 1):
+            assert m.block_step(side, k) == 0
+            assert oracle.halfstep(P, side, k, W, H, yhat) == 0
+            Wg, Hg = m.factors()
+            assert rel_embed_err(Wg, W) <= STEP_TOL, (k, side)
+            assert rel_embed_err(Hg, H) <= STEP_TOL, (k, side)
+    e = m.residuals().astype(np.float64)
+    scale = np.abs(yhat - yref).max()
+    assert np.abs(e - (yhat - yref)).max() <= STEP_TOL * scale
+
+
+def test_long_rows_are_split_and_still_exact():
+    """A user with every item and an item with every user exceed the split length."""
+    n_users, n_items, d, b = 700, 600, 16, 8
+    rng = np.random.default_rng(3)
+    mask = rng.random((n_users, n_items)) < 0.02
+    mask[5, :] = True
+    mask[:, 7] = True
+    u, i = np.nonzero(mask)
+    data = synth.from_pairs(n_users, n_items, u, i)
+    W0, H0 = synth.init_factors(n_users, n_items, d, 0.05, 3)
+    m = Model(data, d, b, 0.1, 1e-3, 0.2, W0=W0, H0=H0)
+    o, st = m.epoch(2, objective=True)
+    assert st == 0
+    P = oracle.Problem.from_data(data, d, b, 0.1, 1e-3, 0.2)
+    Wr, Hr, _, _, st = oracle.ialspp(P, 2, W0, H0)
+    W, H = m.factors()
+    assert abs(o - oracle.objective(P, Wr, Hr)) <= OBJ_TOL * abs(o)
+    assert rel_embed_err(W, Wr) <= EMB_TOL and rel_embed_err(H, Hr) <= EMB_TOL
+
+
+def test_b_equals_d_is_closed_form_ials():
+    prob = small(d=16, seed=4)
+    m = Model(prob.data, 16, 16, 0.1, 1e-3, 0.0, W0=prob.W0, H0=prob.H0)
+    m.epoch(1)
+    W, H = m.factors()
+    P = oracle.Problem.from_data(prob.data, 16, 16, 0.1, 1e-3, 0.0)
+    Wr, Hr, st = oracle.ials(P, 1, prob.W0, prob.H0)
+    assert rel_embed_err(W, Wr) <= EMB_TOL and rel_embed_err(H, Hr) <= EMB_TOL
+
+
+def test_b_equals_1_is_icd():
+    prob = small(d=8, seed=5)
+    m = Model(prob.data, 8, 1, 0.1, 1e-3, 0.0, W0=prob.W0, H0=prob.H0)
+    m.epoch(2)
+    W, H = m.factors()
+    P = oracle.Problem.from_data(prob.data, 8, 1, 0.1, 1e-3, 0.0)
+    Wr, Hr, _, st = oracle.icd(P, 2, prob.W0, prob.H0)
+    assert rel_embed_err(W, Wr) <= EMB_TOL and rel_embed_err(H, Hr) <= EMB_TOL
+
+
+def test_objective_matches_oracle():
+    prob = small(d=64, seed=6)
+    y, a = weights(prob.data.nnz, 6)
+    m = Model(prob.data, 64, 16, 0.3, 0.01, 0.7, y=y, alpha=a)
+    rng = np.random.default_rng(6)
+    W = rng.normal(0, 0.2, (prob.data.n_users, 64)).astype(np.float32)
+    H = rng.normal(0, 0.2, (prob.data.n_items, 64)).astype(np.float32)
+    m.set_factors(W, H)
+    P = oracle.Problem.from_data(prob.data, 64, 16, 0.3, 0.01, 0.7, y=y, alpha=a)
+    ref = oracle.objective(P, W, H)
+    assert abs(m.objective() - ref) <= 1e-6 * abs(ref)
+
+
+def test_residual_cache_stays_consistent():
+    prob = small(d=32, seed=7)
+    m = Model(prob.data, 32, 8, 0.1, 1e-3, W0=prob.W0, H0=prob.H0)
+    m.epoch(2)
+    e_kept = m.residuals()
+    m.recompute_residuals()
+    e_new = m.residuals()
+    assert np.abs(e_kept - e_new).max() <= 1e-5 * max(1.0, np.abs(e_new).max())
+
+
+def test_fp64_retry_path_gives_the_same_answer():
+    prob = small(d=16, seed=8)
+    data = prob.data
+    a = Model(data, 16, 8, 0.1, 1e-3, W0=prob.W0, H0=prob.H0)
+    b = Model(data, 16, 8, 0.1, 1e-3, W0=prob.W0, H0=prob.H0, force_fp64=True)
+    a.epoch(1)
+    _, st = b.epoch(1)
+    assert st == 0
+    retries, not_pd = b.stats()
+    assert retries == (data.n_users + data.n_items) * 2 and not_pd == 0
+    assert a.stats() == (0, 0)
+    Wa, Ha = a.factors()
+    Wb, Hb = b.factors()
+    assert rel_embed_err(Wb, Wa) <= STEP_TOL and rel_embed_err(Hb, Ha) <= STEP_TOL
+    P = oracle.Problem.from_data(data, 16, 8, 0.1, 1e-3)
+    Wr, Hr, _, _, _ = oracle.ialspp(P, 1, prob.W0, prob.H0)
+    assert rel_embed_err(Wb, Wr) <= EMB_TOL
+
+
+def test_singular_rows_are_reported_and_left_unchanged():
+    # lambda = alpha0 = 0: a user with no interactions has the zero Hessian.
+    n_users, n_items, d, b = 50, 40, 8, 4
+    rng = np.random.default_rng(9)
+    mask = rng.random((n_users, n_items)) < 0.3
+    mask[0, :] = False
+    u, i = np.nonzero(mask)
+    data = synth.from_pairs(n_users, n_items, u, i)
+    W0, H0 = synth.init_factors(n_users, n_items, d, 0.1, 9)
+    m = Model(data, d, b, 0.0, 0.0, 0.0, W0=W0, H0=H0)
+    st = m.block_step(0, 0)
+    assert st == _abi.ENOTPD
+    W, _ = m.factors()
+    np.testing.assert_array_equal(W[0], W0[0])
+    assert m.stats()[1] >= 1
+
+
+def test_empty_interaction_set():
+    n_users, n_items, d, b = 5, 4, 8, 4
+    data = synth.from_pairs(n_users, n_items, [], [])
+    W0, H0 = synth.init_factors(n_users, n_items, d, 0.3, 10)
+    m = Model(data, d, b, 0.2, 0.05, W0=W0, H0=H0)
+    o, st = m.epoch(1, objective=True)
+    assert st == 0
+    P = oracle.Problem.from_data(data, d, b, 0.2, 0.05)
+    Wr, Hr, _, _, _ = oracle.ialspp(P, 1, W0, H0)
+    W, H = m.factors()
+    assert rel_embed_err(W, Wr) <= EMB_TOL and rel_embed_err(H, Hr) <= EMB_TOL
+    assert abs(o - oracle.objective(P, Wr, Hr)) <= OBJ_TOL * abs(o)
+
+
+def test_deterministic_and_graph_replay_bitwise():
+    prob = small(d=32, seed=11)
+    runs = []
+    for graph in (False, False, True):
+        m = Model(prob.data, 32, 32, 0.1, 1e-3, 1.0, W0=prob.W0, H0=prob.H0, graph=graph)
+        m.epoch(2)
+        runs.append(m.factors())
+        m.close()
+    for W, H in runs[1:]:
+        np.testing.assert_array_equal(W, runs[0][0])
+        np.testing.assert_array_equal(H, runs[0][1])
+
+
+def test_checkpoint_resume_is_bitwise():
+    prob = small(d=16, seed=12)
+    a = Model(prob.data, 16, 8, 0.1, 1e-3, W0=prob.W0, H0=prob.H0)
+    a.epoch(3)
+    b = Model(prob.data, 16, 8, 0.1, 1e-3, W0=prob.W0, H0=prob.H0)
+    b.epoch(1)
+    W1, H1 = b.factors()
+    b.close()
+    c = Model(prob.data, 16, 8, 0.1, 1e-3, W0=W1, H0=H1)
+    c.epoch(2)
+    for x, y in zip(a.factors(), c.factors()):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_partial_gramian_entry_point():
+    import torch
+    rng = np.random.default_rng(13)
+    for n, d, p0, bs in [(1, 4, 0, 4), (1000, 16, 8, 8), (20011, 128, 32, 32), (5000, 256, 0, 64)]:
+        X = rng.normal(0, 1, (n, d)).astype(np.float32)
+        Xt = torch.from_numpy(X).cuda()
+        G = torch.empty((d, bs), dtype=torch.float32, device="cuda")
+        _abi.ials_partial_gramian(Xt, n, d, p0, bs, G)
+        ref = X.astype(np.float64).T @ X[:, p0:p0 + bs].astype(np.float64)
+        err = np.abs(G.cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert err <= 1e-5, (n, d, err)
+
+
+def test_bad_inputs_rejected():
+    prob = small(d=16, seed=14)
+    data = prob.data
+    bad = data.u_items.copy()
+    bad[1] = bad[0] if data.u_indptr[1] > 1 else data.n_items  # repeat or out of range
+    with pytest.raises(_abi.IalsError) as ei:
+        _abi.ials_create(_abi.make_params(16, 8, 0.1, 1e-3), data.n_users, data.n_items,
+                         data.u_indptr, bad)
+    assert ei.value.status == _abi.EINVAL
+    wrong_t = data.i_users.copy()
+    wrong_t[0] = (wrong_t[0] + 1) % data.n_users
+    with pytest.raises(_abi.IalsError) as ei:
+        _abi.ials_create(_abi.make_params(16, 8, 0.1, 1e-3), data.n_users, data.n_items,
+                         data.u_indptr, data.u_items, data.i_indptr, wrong_t)
+    assert ei.value.status == _abi.EINVAL
+
+
+# --------------------------------------------------------- full-size sampled parity
+
+@pytest.fixture(scope="module")
+def ml20m():
+    return synth.preset("ml20m_136k", seed=0)
+
+
+def test_full_size_sampled_rows(ml20m):
+    """136k x 20k, 10M positives, d=128, b=32: one user step and one item step.
+
+    The oracle recomputes sampled rows (including the longest, split ones) one by
+    one from the same pre-step state; the whole step is also checked through the
+    maintained residual cache.
+    """
+    prob = ml20m
+    data = prob.data
+    m = Model(data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu, W0=prob.W0, H0=prob.H0)
+    P = oracle.Problem.from_data(data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu)
+    rng = np.random.default_rng(0)
+    for side, block in ((0, 0), (1, 0), (0, 3), (1, 3)):
+        W, H = m.factors()
+        e = m.residuals().astype(np.float64)
+        yhat = e + 1.0
+        ptr = data.u_indptr if side == 0 else data.i_indptr
+        lens = np.diff(ptr)
+        n_rows = lens.size
+        rows = np.unique(np.concatenate([np.argsort(-lens)[:6], rng.integers(0, n_rows, 120)]))
+        st, ref = oracle.rows_step(P, side, block, W, H, yhat, rows)
+        assert np.all(st == 0)
+        assert m.block_step(side, block) == 0
+        W2, H2 = m.factors()
+        got = (W2 if side == 0 else H2)[rows, block * prob.b:(block + 1) * prob.b]
+        err = np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-12)
+        assert err.max() <= EMB_TOL, (side, block, err.max())
+    # the maintained cache still matches the model after four steps
+    e_kept = m.residuals()
+    m.recompute_residuals()
+    assert np.abs(e_kept - m.residuals()).max() <= 1e-4
+
+
+def test_full_size_objective_never_increases(ml20m):
+    prob = ml20m
+    m = Model(prob.data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu, W0=prob.W0, H0=prob.H0,
+              graph=True)
+    prev = m.objective()
+    for _ in range(2):
+        o, st = m.epoch(1, objective=True)
+        assert st == 0
+        assert o <= prev * (1 + 1e-6)
+        prev = o

@@ -356,3 +356,16 @@ def test_bad_transpose_is_rejected():
     with pytest.raises(ValueError):
         oracle.Problem(data.n_users, data.n_items, data.u_indptr, data.u_items, data.i_indptr,
                        bad, 6, 2, 0.1, 0.1)
+
+
+def test_rows_step_matches_row_step():
+    data, y, alpha, W, H = tiny(n_users=20, n_items=12, d=6, seed=17)
+    P = make(data, y, alpha, 6, 2, 0.2, 0.05, 0.3)
+    W1, H1 = P.factors(W, H)
+    yhat = oracle.predict(P, W1, H1)
+    rows = np.array([3, 0, 11, 5])
+    st, out = oracle.rows_step(P, 1, 2, W1, H1, yhat, rows)
+    for k, r in enumerate(rows):
+        s1, w1 = oracle.row_step(P, 1, 2, W1, H1, yhat, r)
+        assert st[k] == s1 == 0
+        np.testing.assert_array_equal(out[k], w1)
