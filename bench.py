@@ -183,7 +183,7 @@ def run_ours(args):
     prob = synth.preset(WORKLOAD, seed=0)
     data = prob.data
     prec = _abi.PREC_BF16 if args.precision == "bf16" else _abi.PREC_FP32
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
     m = ials.Model(data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu, precision=prec,
                    graph=not args.no_graph, stream=stream, W0=prob.W0, H0=prob.H0)
     rows_per_epoch = (data.n_users + data.n_items) * (prob.d // prob.b)

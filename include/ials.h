@@ -23,8 +23,9 @@
  *    of its arrays.  The library owns W, H, residuals and all workspaces until
  *    ials_destroy / ials_foldin_close.
  *  - Matrices are row-major float32: W is n_users x d, H is n_items x d.
- *  - All device work of a context runs on the stream given at creation (NULL
- *    means the legacy default stream).  Calls on one context must not overlap
+ *  - All device work of a context runs on the stream given at creation (NULL:
+ *    a private stream that orders with the legacy default stream; the legacy
+ *    stream itself cannot be captured into a CUDA graph).  Calls on one context must not overlap
  *    (a context is single-threaded); submit/poll on a fold-in server are
  *    thread-safe.
  *  - The library runs on the current CUDA device at creation time; it needs an
@@ -87,7 +88,7 @@ typedef struct {
  * within a row), else IALS_EINVAL.  If NULL the library builds it.
  * y and alpha are per interaction in user-major order; NULL means all ones
  * (binary implicit feedback).  alpha must be > 0.
- * nnz must be < 2^31.  cuda_stream is a cudaStream_t (NULL = default stream).
+ * nnz must be < 2^31.  cuda_stream is a cudaStream_t (see the stream convention above).
  * On success *out receives the context; W and H hold the seeded initial draw. */
 ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_items,
                         int64_t nnz, const int64_t *u_indptr, const int32_t *u_items,
@@ -110,8 +111,9 @@ ials_status ials_objective(ials_ctx *ctx, double *out);
 /* Copy W (n_users x d) and/or H (n_items x d) out; either pointer may be NULL. */
 ials_status ials_get_factors(ials_ctx *ctx, float *W, float *H);
 
-/* Overwrite W and/or H (either may be NULL); used to resume from a checkpoint
- * taken at an epoch boundary (Algorithm 3 recomputes the cache per epoch). */
+/* Overwrite W and/or H (either may be NULL) and recompute the residual cache
+ * from them; used to resume from a checkpoint taken at an epoch boundary
+ * (Algorithm 3 recomputes the cache per epoch, so resuming is exact). */
 ials_status ials_set_factors(ials_ctx *ctx, const float *W, const float *H);
 
 /* --- single steps of Algorithm 3 (for step-level checks and profiling) --- */

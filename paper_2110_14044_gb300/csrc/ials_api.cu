@@ -38,6 +38,7 @@ ials_status fail(ials_status st, const std::string &msg) {
 
 ials_status cuda_fail(cudaError_t e, const char *what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();  // do not leak a non-sticky error into the next call
     return IALS_ECUDA;
 }
 
@@ -125,6 +126,7 @@ struct ials_ctx {
     int32_t n_obj_part = 0;
     double *g64a = nullptr, *g64b = nullptr, *g64ws = nullptr;
     cudaGraphExec_t graph = nullptr;
+    bool own_stream = false;
     // per side, for the work model: interactions in unsplit rows / split rows,
     // number of unsplit rows, split rows, partial slots, tasks
     int64_t nnz_unsplit[2] = {0, 0}, nnz_split[2] = {0, 0};
@@ -147,6 +149,7 @@ struct ials_ctx {
     ~ials_ctx() {
         if (graph) cudaGraphExecDestroy(graph);
         for (auto &b : bufs) cudaFree(b.p);
+        if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
 
@@ -397,6 +400,13 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     c->nnz = nnz;
     c->device = dev;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (!c->stream) {
+        // The legacy default stream cannot be captured into a graph: use a
+        // private stream that still orders with it (a blocking stream).
+        cudaError_t se = cudaStreamCreate(&c->stream);
+        if (se != cudaSuccess) { c->stream = nullptr; delete c; return cuda_fail(se, "stream"); }
+        c->own_stream = true;
+    }
 
     // ---- work decomposition
     const int64_t split_len = std::max<int64_t>(256, std::min<int64_t>(8192, nnz / (152 * 16 * 2)));
@@ -565,6 +575,10 @@ ials_status ials_set_factors(ials_ctx *c, const float *W, const float *H) {
     const size_t wb = sizeof(float) * (size_t)c->n_users * c->p.d, hb = sizeof(float) * (size_t)c->n_items * c->p.d;
     if (W) IALS_CUDA(cudaMemcpyAsync(c->W, W, wb, cudaMemcpyDefault, c->stream), "copy W in");
     if (H) IALS_CUDA(cudaMemcpyAsync(c->H, H, hb, cudaMemcpyDefault, c->stream), "copy H in");
+    // the residual cache is a function of W and H: keep it consistent
+    IALS_CUDA(launch_residual(c->side[0].ptr, c->side[0].idx, c->W, c->H, c->y, c->n_users,
+                              c->p.d, c->e, c->stream),
+              "residual recompute");
     IALS_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
     return IALS_OK;
 }

@@ -326,3 +326,11 @@ def test_full_size_objective_never_increases(ml20m):
         assert st == 0
         assert o <= prev * (1 + 1e-6)
         prev = o
+
+
+def test_set_factors_refreshes_residual_cache():
+    prob = small(d=16, seed=15)
+    m = Model(prob.data, 16, 8, 0.1, 1e-3, W0=prob.W0, H0=prob.H0)
+    e = m.residuals()
+    P = oracle.Problem.from_data(prob.data, 16, 8, 0.1, 1e-3)
+    np.testing.assert_allclose(e, oracle.predict(P, prob.W0, prob.H0) - 1.0, rtol=1e-5, atol=1e-6)
