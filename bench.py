@@ -295,6 +295,23 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_ncu_step(args):
+    """One user and one item block step (block 0) on the bench workload, for ncu."""
+    import torch
+    from paper_2110_14044_gb300 import _abi, build, synth
+    build.build()
+    import paper_2110_14044_gb300 as ials
+    prob = synth.preset(WORKLOAD, seed=0)
+    prec = _abi.PREC_BF16 if args.precision == "bf16" else _abi.PREC_FP32
+    m = ials.Model(prob.data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu, precision=prec,
+                   W0=prob.W0, H0=prob.H0)
+    for side in (0, 1):
+        assert m.block_step(side, 0) == 0
+    torch.cuda.synchronize()
+    m.close()
+    print("ncu-step done")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,8 +321,12 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-step", action="store_true",
+                    help="run one user and one item block step only (for profiler captures)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.ncu_step:
+        run_ncu_step(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

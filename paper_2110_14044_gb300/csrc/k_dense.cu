@@ -23,7 +23,8 @@ __device__ __forceinline__ float dot4(float4 a, float4 b) {
 // ------------------------------------------------------------------ residual
 // One warp per user row.  The warp is split into sub-groups of SG lanes; each
 // sub-group handles one interaction at a time, lane l of the sub-group owning
-// float4 chunks l, l + SG, ... of the d-vector.  MAXV bounds those chunks.
+// float4 chunks l, l + SG, ... (MAXV of them) of the d-vector.  Each sub-group
+// keeps two interactions in flight (independent gathers) per iteration.
 // LOSS = false: write e[s] = <w_u, h_i> - y_s.
 // LOSS = true : accumulate alpha_s (<w_u, h_i> - y_s)^2 in FP64, one partial per block.
 template <int MAXV, bool LOSS>
@@ -51,26 +52,37 @@ __global__ void __launch_bounds__(256) k_residual(const int64_t *__restrict__ u_
             wv[m] = v < nv4 ? W4[(int64_t)u * nv4 + v] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const int64_t beg = u_ptr[u], end = u_ptr[u + 1];
-        for (int64_t s0 = beg; s0 < end; s0 += nsub) {
-            const int64_t s = s0 + sub;
-            const bool valid = s < end;
-            float acc = 0.f;
-            if (valid) {
-                const int64_t c = u_idx[s];
+        for (int64_t s0 = beg; s0 < end; s0 += 2 * nsub) {
+            const int64_t s1 = s0 + sub, s2 = s0 + nsub + sub;
+            const bool v1 = s1 < end, v2 = s2 < end;
+            const int64_t c1 = v1 ? u_idx[s1] : 0, c2 = v2 ? u_idx[s2] : 0;
+            float a1 = 0.f, a2 = 0.f;
+            float4 h1[MAXV], h2[MAXV];
 #pragma unroll
-                for (int m = 0; m < MAXV; ++m) {
-                    const int v = sl + m * SG;
-                    if (v < nv4) acc += dot4(wv[m], H4[c * nv4 + v]);
-                }
+            for (int m = 0; m < MAXV; ++m) {
+                const int v = sl + m * SG;
+                h1[m] = (v1 && v < nv4) ? __ldg(H4 + c1 * nv4 + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+                h2[m] = (v2 && v < nv4) ? __ldg(H4 + c2 * nv4 + v) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            for (int o = SG >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-            if (valid && sl == 0) {
-                const float r = acc - (y ? y[s] : 1.0f);
-                if (LOSS) {
-                    const double a = alpha ? (double)alpha[s] : 1.0;
-                    loss += a * (double)r * (double)r;
-                } else {
-                    e[s] = r;
+#pragma unroll
+            for (int m = 0; m < MAXV; ++m) {
+                a1 += dot4(wv[m], h1[m]);
+                a2 += dot4(wv[m], h2[m]);
+            }
+            for (int o = SG >> 1; o > 0; o >>= 1) {
+                a1 += __shfl_xor_sync(kFull, a1, o);
+                a2 += __shfl_xor_sync(kFull, a2, o);
+            }
+            if (sl == 0) {
+                if (v1) {
+                    const float r = a1 - (y ? y[s1] : 1.0f);
+                    if (LOSS) loss += (alpha ? (double)alpha[s1] : 1.0) * (double)r * (double)r;
+                    else e[s1] = r;
+                }
+                if (v2) {
+                    const float r = a2 - (y ? y[s2] : 1.0f);
+                    if (LOSS) loss += (alpha ? (double)alpha[s2] : 1.0) * (double)r * (double)r;
+                    else e[s2] = r;
                 }
             }
         }
@@ -323,9 +335,10 @@ cudaError_t launch_residual_impl(const int64_t *u_ptr, const int32_t *u_idx, con
                                  const float *H, const float *y, const float *alpha,
                                  int32_t n_users, int32_t d, float *e, double *part,
                                  int grid, cudaStream_t s) {
+    // sub-group size: about four float4 chunks per lane, at most 32 lanes
     const int nv4 = d / 4;
     int sg_log = 0;
-    while ((2 << sg_log) <= nv4 && (2 << sg_log) <= 32) ++sg_log;
+    while ((2 << sg_log) <= 32 && (2 << sg_log) * 4 <= nv4) ++sg_log;
     const int SG = 1 << sg_log;
     const int maxv = (nv4 + SG - 1) / SG;
 #define IALS_RES(MV)                                                                         \

@@ -287,6 +287,274 @@ __global__ void __launch_bounds__(256, 2) k_sparse(const StepArgs a) {
     }
 }
 
+// ------------------------------------------------- tiled kernel, B = 8, 16, 32
+// Same step as k_sparse, with the b x b statistics accumulated in registers by
+// lane tiles.  A_r is cut into a 4 x 4 grid of T x T tiles (T = B / 4); only
+// the 10 tiles on or below the diagonal are formed.  Lane l < 30 belongs to
+// interaction group grp = l / 10 (the three groups take interactions k = grp,
+// grp + 3, ...) and owns tile t = l % 10, so every staged interaction costs a
+// lane T*T FMAs with 2 T / 4 shared loads.  The three group partials are summed
+// in a fixed order into a shared copy of A_r, whose rows then feed the same
+// warp Cholesky as k_sparse.  Slices are gathered with cp.async into two
+// staging buffers, so the next 32 interactions load while the current ones are
+// multiplied.
+template <int B>
+struct TileCfg {
+    static constexpr int T = B / 4;
+    static constexpr int NT = 10, NG = 3, ACTIVE = NT * NG;
+    static constexpr int SB = B + 4;
+    static constexpr int CH = 32;
+    static constexpr int BUF = CH * SB;
+    static constexpr int VEC = (B + 3) / 4 * 4;
+    static constexpr int WARP_FLOATS = 2 * BUF + 4 * CH + 2 * VEC;
+    static constexpr int WARPS = 8;
+    static constexpr int SMEM_BYTES = (B * B + WARPS * WARP_FLOATS) * 4;
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Issue the gathers of `cnt` slices (column id of slice k held by lane k) into buf.
+template <int B>
+__device__ __forceinline__ void gather_async(float *buf, const float *__restrict__ F, int d, int p0,
+                                             int c_lane, int cnt, int lane) {
+    constexpr int SB = TileCfg<B>::SB;
+    constexpr int VPR = B / 4, RPP = 32 / VPR, NP = 32 / RPP;
+    const int v = lane % VPR, rr = lane / VPR;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int k = p * RPP + rr;
+        const int ck = __shfl_sync(kFull, c_lane, k);
+        if (k < cnt) cp_async16(buf + k * SB + 4 * v, F + (int64_t)ck * d + p0 + 4 * v);
+    }
+}
+
+template <int T>
+__device__ __forceinline__ void load_seg(const float *p, float (&x)[T]) {
+    if constexpr (T % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < T; i += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(p + i);
+            x[i] = v.x; x[i + 1] = v.y; x[i + 2] = v.z; x[i + 3] = v.w;
+        }
+    } else {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        x[0] = v.x; x[1] = v.y;
+    }
+}
+
+template <int T>
+__device__ __forceinline__ void store_tile(float *p, const float (&x)[T], bool add) {
+    if constexpr (T % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < T; i += 4) {
+            float4 v = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
+            if (add) {
+                const float4 o = *reinterpret_cast<const float4 *>(p + i);
+                v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+            }
+            *reinterpret_cast<float4 *>(p + i) = v;
+        }
+    } else {
+        float2 v = make_float2(x[0], x[1]);
+        if (add) {
+            const float2 o = *reinterpret_cast<const float2 *>(p);
+            v.x += o.x; v.y += o.y;
+        }
+        *reinterpret_cast<float2 *>(p) = v;
+    }
+}
+
+template <int B, bool PERM, bool HAS_A>
+__global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
+    using C = TileCfg<B>;
+    constexpr int T = C::T, SB = C::SB, CH = C::CH;
+    extern __shared__ float4 smem4[];
+    float *smem = reinterpret_cast<float *>(smem4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *sGpp = smem;
+    for (int i = threadIdx.x; i < B * B; i += blockDim.x)
+        sGpp[i] = a.alpha0 * a.G[(int64_t)(a.p0 + i / B) * B + (i % B)];
+    float *wbase = smem + B * B + warp * C::WARP_FLOATS;
+    // buffer bi (0 or 1): slices at wbase + bi * BUF, residuals at she + bi * CH,
+    // weights at sha + bi * CH
+    float *const she = wbase + 2 * C::BUF;
+    float *const sha = she + 2 * CH;
+    float *gs = wbase + 2 * C::BUF + 4 * CH;   // gradient (B)
+    float *vv = gs + C::VEC;                   // delta / Cholesky column (B)
+    for (int i = lane; i < C::BUF; i += 32) wbase[C::BUF + i] = 0.f;  // finite values above the diagonal
+    __syncthreads();
+    WarpSmem w;
+    w.v = vv;
+    w.L = wbase + C::BUF;  // the factor copy reuses the second staging buffer
+    const int col = lane % B, sub = lane / B;
+    const bool active = lane < C::ACTIVE;
+    const int grp = active ? lane / C::NT : C::NG, t = lane % C::NT;
+    const int ti = t >= 6 ? 3 : (t >= 3 ? 2 : (t >= 1 ? 1 : 0));
+    const int tj = t - ti * (ti + 1) / 2;
+    for (;;) {
+        int tsk = 0;
+        if (lane == 0) tsk = atomicAdd(a.counter, 1);
+        tsk = __shfl_sync(kFull, tsk, 0);
+        if (tsk >= a.n_tasks) break;
+        const Task tk = a.tasks[tsk];
+        const int nch = (tk.len + CH - 1) / CH;
+        float acc[T][T], gacc[T];
+#pragma unroll
+        for (int i = 0; i < T; ++i) {
+            gacc[i] = 0.f;
+#pragma unroll
+            for (int j = 0; j < T; ++j) acc[i][j] = 0.f;
+        }
+        // chunk meta in registers: column id, residual index, residual, weight
+        int cB = 0;
+        int64_t qB = 0, q0 = 0;
+        float eB = 0.f, aB = 1.f;
+        auto load_meta = [&](int j) {
+            const int cnt = min(CH, tk.len - j * CH);
+            if (lane < cnt) {
+                const int64_t s = tk.begin + (int64_t)j * CH + lane;
+                cB = a.idx[s];
+                qB = PERM ? (int64_t)a.pos[s] : s;
+                eB = a.e[qB];
+                if (HAS_A) aB = a.alpha[qB];
+            }
+        };
+        auto issue = [&](int j, int bi) {
+            const int cnt = min(CH, tk.len - j * CH);
+            gather_async<B>(wbase + bi * C::BUF, a.F, a.d, a.p0, cB, cnt, lane);
+            she[bi * CH + lane] = HAS_A ? aB * eB : eB;
+            if (HAS_A) sha[bi * CH + lane] = aB;
+            cp_async_commit();
+        };
+        if (nch > 0) {
+            load_meta(0);
+            q0 = qB;
+            issue(0, 0);
+            if (nch > 1) load_meta(1);
+        }
+        for (int ch = 0; ch < nch; ++ch) {
+            const int bi = ch & 1;
+            cp_async_wait_all();
+            __syncwarp();
+            if (ch + 1 < nch) {
+                issue(ch + 1, bi ^ 1);
+                if (ch + 2 < nch) load_meta(ch + 2);
+            }
+            const int cnt = min(CH, tk.len - ch * CH);
+            const float *bp = wbase + bi * C::BUF;
+            const float *be = she + bi * CH;
+            const float *ba = sha + bi * CH;
+            for (int k = grp; k < cnt; k += C::NG) {
+                const float *xk = bp + k * SB;
+                float xa[T], xb[T];
+                load_seg<T>(xk + T * ti, xa);
+                load_seg<T>(xk + T * tj, xb);
+                const float ek = be[k];
+#pragma unroll
+                for (int i = 0; i < T; ++i) gacc[i] += ek * xa[i];
+                if (HAS_A) {
+                    const float ak = ba[k];
+#pragma unroll
+                    for (int i = 0; i < T; ++i) xa[i] *= ak;
+                }
+#pragma unroll
+                for (int i = 0; i < T; ++i)
+#pragma unroll
+                    for (int j = 0; j < T; ++j) acc[i][j] += xa[i] * xb[j];
+            }
+            __syncwarp();
+        }
+        // fixed-order sum of the three group partials into the shared A_r (buffer 1)
+        float *As = wbase + C::BUF;
+#pragma unroll
+        for (int ph = 0; ph < C::NG; ++ph) {
+            if (grp == ph) {
+#pragma unroll
+                for (int i = 0; i < T; ++i) store_tile<T>(As + (T * ti + i) * SB + T * tj, acc[i], ph > 0);
+                if (tj == 0) {
+#pragma unroll
+                    for (int i = 0; i < T; ++i) gs[T * ti + i] = (ph > 0 ? gs[T * ti + i] : 0.f) + gacc[i];
+                }
+            }
+            __syncwarp();
+        }
+        float A[B];
+#pragma unroll
+        for (int j = 0; j < B; j += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(As + col * SB + j);
+            A[j] = v.x; A[j + 1] = v.y; A[j + 2] = v.z; A[j + 3] = v.w;
+        }
+        float g = gs[col];
+        __syncwarp();
+        if (tk.slot >= 0) {  // a chunk of a long row: store the partial statistics (row col)
+            if (sub == 0) {
+                float *P = a.part + (int64_t)tk.slot * (B * B + B);
+#pragma unroll
+                for (int j = 0; j < B; j += 4)
+                    *reinterpret_cast<float4 *>(P + col * B + j) = make_float4(A[j], A[j + 1], A[j + 2], A[j + 3]);
+                P[B * B + col] = g;
+            }
+            continue;
+        }
+        const int row = tk.row;
+        const float lam = a.lambda * (1.0f + a.nu * (float)tk.len);
+#pragma unroll
+        for (int j = 0; j < B; ++j) A[j] += sGpp[col * B + j] + (j == col ? lam : 0.f);
+        g += a.R[(int64_t)row * B + col];
+        float delta;
+        if (!chol_solve<B>(A, g, col, sub, w, a.force_fp64 != 0, delta)) {
+            queue_retry(a, lane, row);
+            continue;
+        }
+        if (sub == 0) a.X[(int64_t)row * a.d + a.p0 + col] -= delta;
+        __syncwarp();
+        if (sub == 0) vv[col] = delta;
+        __syncwarp();
+        if (nch == 1) {  // the slices are still in buffer 0
+            if (lane < tk.len) a.e[q0] -= dot_slice<B>(vv, wbase + lane * SB);
+            __syncwarp();
+        } else if (nch > 1) {
+            int64_t qc = 0;
+            // meta one chunk ahead, slices double-buffered
+            auto meta2 = [&](int j) {
+                const int cnt = min(CH, tk.len - j * CH);
+                if (lane < cnt) {
+                    const int64_t s = tk.begin + (int64_t)j * CH + lane;
+                    cB = a.idx[s];
+                    qB = PERM ? (int64_t)a.pos[s] : s;
+                }
+            };
+            meta2(0);
+            qc = qB;
+            gather_async<B>(wbase, a.F, a.d, a.p0, cB, min(CH, tk.len), lane);
+            cp_async_commit();
+            meta2(1);
+            for (int ch = 0; ch < nch; ++ch) {
+                const int bi = ch & 1;
+                cp_async_wait_all();
+                __syncwarp();
+                int64_t qn = 0;
+                if (ch + 1 < nch) {
+                    gather_async<B>(wbase + (bi ^ 1) * C::BUF, a.F, a.d, a.p0, cB,
+                                    min(CH, tk.len - (ch + 1) * CH), lane);
+                    cp_async_commit();
+                    qn = qB;
+                    if (ch + 2 < nch) meta2(ch + 2);
+                }
+                const int cnt = min(CH, tk.len - ch * CH);
+                if (lane < cnt) a.e[qc] -= dot_slice<B>(vv, wbase + bi * C::BUF + lane * SB);
+                __syncwarp();
+                qc = qn;
+            }
+        }
+    }
+}
+
 // One warp per split row: sum the partial slots in order, add the dense terms, solve, apply.
 template <int B>
 __global__ void __launch_bounds__(256) k_split_solve(const StepArgs a) {
@@ -306,7 +574,7 @@ __global__ void __launch_bounds__(256) k_split_solve(const StepArgs a) {
         for (int sl = 0; sl < sr.nslots; ++sl) {
             const float *P = a.part + (int64_t)(sr.slot0 + sl) * (B * B + B);
 #pragma unroll
-            for (int j = 0; j < B; ++j) acc[j] += P[j * B + col];
+            for (int j = 0; j < B; ++j) acc[j] += P[col * B + j];
             g += P[B * B + col];
         }
         const float lam = a.lambda * (1.0f + a.nu * (float)sr.len);
@@ -456,13 +724,21 @@ __global__ void __launch_bounds__(128) k_retry(const StepArgs a) {
 }
 
 template <int B, bool PERM, bool HAS_A>
+constexpr auto main_kernel() {
+    if constexpr (B >= 8) return k_sparse_tiled<B, PERM, HAS_A>;
+    else return k_sparse<B, PERM, HAS_A>;
+}
+
+template <int B, bool PERM, bool HAS_A>
 cudaError_t launch_step_b(const StepArgs &a, cudaStream_t s) {
     using C = SparseCfg<B>;
+    constexpr bool TILED = B >= 8;
+    auto kmain = main_kernel<B, PERM, HAS_A>();
+    constexpr int MAIN_SMEM = TILED ? TileCfg<(B >= 8 ? B : 8)>::SMEM_BYTES : C::SMEM_BYTES;
     static bool attr_done = false;
     static int per_sm = 0;
     if (!attr_done) {
-        cudaError_t e1 = cudaFuncSetAttribute(k_sparse<B, PERM, HAS_A>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+        cudaError_t e1 = cudaFuncSetAttribute(kmain, cudaFuncAttributeMaxDynamicSharedMemorySize, MAIN_SMEM);
         cudaError_t e2 = cudaFuncSetAttribute(k_split_solve<B>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
         cudaError_t e3 = cudaFuncSetAttribute(k_split_resid<B, PERM>,
@@ -471,7 +747,7 @@ cudaError_t launch_step_b(const StepArgs &a, cudaStream_t s) {
         if (e2 != cudaSuccess) return e2;
         if (e3 != cudaSuccess) return e3;
         cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, k_sparse<B, PERM, HAS_A>, C::WARPS * 32, C::SMEM_BYTES);
+            &per_sm, kmain, C::WARPS * 32, MAIN_SMEM);
         if (err != cudaSuccess) return err;
         if (per_sm < 1) per_sm = 1;
         attr_done = true;
@@ -481,7 +757,7 @@ cudaError_t launch_step_b(const StepArgs &a, cudaStream_t s) {
     if (grid > need) grid = need > 0 ? need : 1;
     if (a.n_tasks > 0) {
         prof_mark(a.prof, K_SPARSE, s);
-        k_sparse<B, PERM, HAS_A><<<grid, C::WARPS * 32, C::SMEM_BYTES, s>>>(a);
+        kmain<<<grid, C::WARPS * 32, MAIN_SMEM, s>>>(a);
         prof_mark(a.prof, -1, s);
     }
     if (a.n_split > 0) {
