@@ -155,20 +155,22 @@ __global__ void k_frobenius(const double *__restrict__ A, const double *__restri
 }
 
 // ------------------------------------------------------------------ Gramian
-// Split-K tile kernel: block (tm, tn, split) accumulates the 64 x 64 output
-// tile [tm*64, +64) x [tn*64, +64) of X^T X[:, p0:p0+bs] over the rows
-// [split*rows_per, +rows_per) of X.  256 threads, 4 x 4 outputs each.
+// Split-K tile kernel: block (tm, tn, split) accumulates the TM x TN output
+// tile [tm*TM, +TM) x [tn*TN, +TN) of X^T X[:, p0:p0+bs] over the rows
+// [split*rows_per, +rows_per) of X.  256 threads, 4 x 4 outputs each; the tile
+// shape follows bs ((256,16), (128,32) or (64,64)) so no thread idles at small b.
 // F64: accumulate each 16-row slab in FP32 and fold it into FP64 accumulators.
-constexpr int GT = 64, GK = 16;
+constexpr int GK = 16;
 
-template <bool F64>
+template <int TM, int TN, bool F64>
 __global__ void __launch_bounds__(256) k_gram_tile(const float *__restrict__ X, int64_t n,
                                                    int32_t d, int32_t p0, int32_t bs,
                                                    int64_t rows_per, void *__restrict__ ws) {
-    __shared__ float As[GK][GT];
-    __shared__ float Bs[GK][GT];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int m0 = blockIdx.x * GT, n0 = blockIdx.y * GT;
+    static_assert((TM / 4) * (TN / 4) == 256, "tile shape");
+    __shared__ __align__(16) float As[GK][TM];
+    __shared__ __align__(16) float Bs[GK][TN];
+    const int tid = threadIdx.x, tx = tid % (TN / 4), ty = tid / (TN / 4);
+    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
     const int64_t k_beg = (int64_t)blockIdx.z * rows_per;
     const int64_t k_end = min(n, k_beg + rows_per);
     float acc[4][4];
@@ -178,12 +180,15 @@ __global__ void __launch_bounds__(256) k_gram_tile(const float *__restrict__ X, 
 #pragma unroll
         for (int j = 0; j < 4; ++j) { acc[i][j] = 0.f; acc64[i][j] = 0.0; }
     for (int64_t k0 = k_beg; k0 < k_end; k0 += GK) {
-        for (int i = tid; i < GK * GT; i += 256) {
-            const int kk = i / GT, mm = i % GT;
+        for (int i = tid; i < GK * TM; i += 256) {
+            const int kk = i / TM, mm = i % TM;
             const int64_t k = k0 + kk;
-            const bool kin = k < k_end;
-            As[kk][mm] = (kin && m0 + mm < d) ? X[k * d + m0 + mm] : 0.f;
-            Bs[kk][mm] = (kin && n0 + mm < bs) ? X[k * d + p0 + n0 + mm] : 0.f;
+            As[kk][mm] = (k < k_end && m0 + mm < d) ? X[k * d + m0 + mm] : 0.f;
+        }
+        for (int i = tid; i < GK * TN; i += 256) {
+            const int kk = i / TN, nn = i % TN;
+            const int64_t k = k0 + kk;
+            Bs[kk][nn] = (k < k_end && n0 + nn < bs) ? X[k * d + p0 + n0 + nn] : 0.f;
         }
         __syncthreads();
 #pragma unroll
@@ -231,14 +236,21 @@ __global__ void k_gram_reduce(const T *__restrict__ ws, int32_t nsplit, int64_t 
 }
 
 struct GramPlan {
-    int tm, tn, nsplit;
+    int tm_size, tn_size, tm, tn, nsplit;
     int64_t rows_per;
 };
 
+inline void tile_shape(int32_t bs, int &TM, int &TN) {
+    if (bs <= 16) { TM = 256; TN = 16; }
+    else if (bs <= 32) { TM = 128; TN = 32; }
+    else { TM = 64; TN = 64; }
+}
+
 GramPlan gram_plan(int64_t n, int32_t d, int32_t bs) {
     GramPlan p;
-    p.tm = (d + GT - 1) / GT;
-    p.tn = (bs + GT - 1) / GT;
+    tile_shape(bs, p.tm_size, p.tn_size);
+    p.tm = (d + p.tm_size - 1) / p.tm_size;
+    p.tn = (bs + p.tn_size - 1) / p.tn_size;
     const int64_t tiles = (int64_t)p.tm * p.tn;
     int64_t ns = (2 * kSMs + tiles - 1) / tiles;
     const int64_t kblocks = (n + GK - 1) / GK;
@@ -251,41 +263,52 @@ GramPlan gram_plan(int64_t n, int32_t d, int32_t bs) {
     return p;
 }
 
+template <bool F64>
+void launch_gram_tiles(const GramPlan &p, const float *X, int64_t n, int32_t d, int32_t p0,
+                       int32_t bs, void *ws, cudaStream_t s) {
+    const dim3 grid(p.tm, p.tn, p.nsplit);
+    if (p.tn_size == 16) k_gram_tile<256, 16, F64><<<grid, 256, 0, s>>>(X, n, d, p0, bs, p.rows_per, ws);
+    else if (p.tn_size == 32) k_gram_tile<128, 32, F64><<<grid, 256, 0, s>>>(X, n, d, p0, bs, p.rows_per, ws);
+    else k_gram_tile<64, 64, F64><<<grid, 256, 0, s>>>(X, n, d, p0, bs, p.rows_per, ws);
+}
+
 // ------------------------------------------------------------------ row terms
 // R[r, f] = alpha0 * sum_k X[r, k] G[k, f] + lambda (1 + nu n_r) X[r, p0 + f]
-// 64 x 64 output tile per block, K = d in slabs of 16.
+// TM x TN output tile per block (rows x coordinates), K = d in slabs of 16.
+template <int TM, int TN>
 __global__ void __launch_bounds__(256) k_rowterm(const float *__restrict__ X,
                                                  const int64_t *__restrict__ ptr, int32_t n_rows,
                                                  int32_t d, int32_t p0, int32_t bs,
                                                  const float *__restrict__ G, float alpha0,
                                                  float lambda, float nu, float *__restrict__ R) {
-    __shared__ float As[GK][GT + 4];
-    __shared__ float Bs[GK][GT];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t r0 = (int64_t)blockIdx.x * GT;
-    const int n0 = blockIdx.y * GT;
+    static_assert((TM / 4) * (TN / 4) == 256, "tile shape");
+    __shared__ __align__(16) float As[GK][TM + 4];
+    __shared__ __align__(16) float Bs[GK][TN];
+    const int tid = threadIdx.x, tx = tid % (TN / 4), ty = tid / (TN / 4);
+    const int64_t r0 = (int64_t)blockIdx.x * TM;
+    const int n0 = blockIdx.y * TN;
     float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
     for (int k0 = 0; k0 < d; k0 += GK) {
-        for (int i = tid; i < GK * GT; i += 256) {
+        for (int i = tid; i < GK * TM; i += 256) {
             const int rr = i / GK, kk = i % GK;
             const int64_t r = r0 + rr;
             const int k = k0 + kk;
             As[kk][rr] = (r < n_rows && k < d) ? X[r * d + k] : 0.f;
-            const int kb = i / GT, nn = i % GT;
+        }
+        for (int i = tid; i < GK * TN; i += 256) {
+            const int kb = i / TN, nn = i % TN;
             Bs[kb][nn] = (k0 + kb < d && n0 + nn < bs) ? G[(int64_t)(k0 + kb) * bs + n0 + nn] : 0.f;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
-            float av[4], bv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+            const float4 a = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
             const float4 b = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
-            bv[0] = b.x; bv[1] = b.y; bv[2] = b.z; bv[3] = b.w;
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -404,7 +427,7 @@ cudaError_t launch_gram(const float *X, int64_t n, int32_t d, int32_t p0, int32_
     const int64_t count = (int64_t)d * bs;
     if (n == 0) return cudaMemsetAsync(G, 0, sizeof(float) * count, s);
     GramPlan p = gram_plan(n, d, bs);
-    k_gram_tile<false><<<dim3(p.tm, p.tn, p.nsplit), 256, 0, s>>>(X, n, d, p0, bs, p.rows_per, ws);
+    launch_gram_tiles<false>(p, X, n, d, p0, bs, ws, s);
     k_gram_reduce<float><<<(unsigned)((count + 255) / 256), 256, 0, s>>>(ws, p.nsplit, count, G);
     return cudaGetLastError();
 }
@@ -419,7 +442,7 @@ cudaError_t launch_gram64(const float *X, int64_t n, int32_t d, double *G64, dou
     const int64_t count = (int64_t)d * d;
     if (n == 0) return cudaMemsetAsync(G64, 0, sizeof(double) * count, s);
     GramPlan p = gram_plan(n, d, d);
-    k_gram_tile<true><<<dim3(p.tm, p.tn, p.nsplit), 256, 0, s>>>(X, n, d, 0, d, p.rows_per, ws);
+    launch_gram_tiles<true>(p, X, n, d, 0, d, ws, s);
     k_gram_reduce<double><<<(unsigned)((count + 255) / 256), 256, 0, s>>>(ws, p.nsplit, count, G64);
     return cudaGetLastError();
 }
@@ -428,8 +451,12 @@ cudaError_t launch_rowterm(const float *X, const int64_t *ptr, int32_t n_rows, i
                            int32_t p0, int32_t bs, const float *G, float alpha0, float lambda,
                            float nu, float *R, cudaStream_t s) {
     if (n_rows == 0) return cudaSuccess;
-    dim3 grid((n_rows + GT - 1) / GT, (bs + GT - 1) / GT);
-    k_rowterm<<<grid, 256, 0, s>>>(X, ptr, n_rows, d, p0, bs, G, alpha0, lambda, nu, R);
+    int TM, TN;
+    tile_shape(bs, TM, TN);
+    dim3 grid((n_rows + TM - 1) / TM, (bs + TN - 1) / TN);
+    if (TN == 16) k_rowterm<256, 16><<<grid, 256, 0, s>>>(X, ptr, n_rows, d, p0, bs, G, alpha0, lambda, nu, R);
+    else if (TN == 32) k_rowterm<128, 32><<<grid, 256, 0, s>>>(X, ptr, n_rows, d, p0, bs, G, alpha0, lambda, nu, R);
+    else k_rowterm<64, 64><<<grid, 256, 0, s>>>(X, ptr, n_rows, d, p0, bs, G, alpha0, lambda, nu, R);
     return cudaGetLastError();
 }
 

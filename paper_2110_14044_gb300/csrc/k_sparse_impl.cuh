@@ -555,43 +555,55 @@ __global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
     }
 }
 
-// One warp per split row: sum the partial slots in order, add the dense terms, solve, apply.
+// One block per split row: 256 threads sum the partial slots of the row in
+// slot order (thread t owns elements t, t + 256, ...), then warp 0 adds the
+// dense terms, solves and applies.
 template <int B>
 __global__ void __launch_bounds__(256) k_split_solve(const StepArgs a) {
-    using C = SparseCfg<B>;
+    constexpr int NE = B * B + B;
     extern __shared__ float4 smem4[];
-    float *smem = reinterpret_cast<float *>(smem4);
+    float *red = reinterpret_cast<float *>(smem4);
+    WarpSmem w;
+    w.v = red + (NE + 3) / 4 * 4;
+    w.L = w.v + (B + 3) / 4 * 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const WarpSmem w = warp_smem<B>(smem, warp);
     const int col = lane % B, sub = lane / B;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < a.n_split; i += nw) {
+    for (int i = blockIdx.x; i < a.n_split; i += gridDim.x) {
         const SplitRow sr = a.split[i];
-        float acc[B];
-#pragma unroll
-        for (int j = 0; j < B; ++j) acc[j] = 0.f;
-        float g = 0.f;
-        for (int sl = 0; sl < sr.nslots; ++sl) {
-            const float *P = a.part + (int64_t)(sr.slot0 + sl) * (B * B + B);
-#pragma unroll
-            for (int j = 0; j < B; ++j) acc[j] += P[col * B + j];
-            g += P[B * B + col];
+        const float *P0 = a.part + (int64_t)sr.slot0 * NE;
+        for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+            float t = 0.f;
+            for (int sl = 0; sl < sr.nslots; ++sl) t += P0[(int64_t)sl * NE + e];
+            red[e] = t;
         }
-        const float lam = a.lambda * (1.0f + a.nu * (float)sr.len);
+        __syncthreads();
+        if (warp == 0) {
+            float acc[B];
 #pragma unroll
-        for (int j = 0; j < B; ++j)
-            acc[j] += a.alpha0 * a.G[(int64_t)(a.p0 + j) * B + col] + (j == col ? lam : 0.f);
-        g += a.R[(int64_t)sr.row * B + col];
-        float delta = 0.f;
-        const bool ok = chol_solve<B>(acc, g, col, sub, w, a.force_fp64 != 0, delta);
-        if (!ok) {
-            queue_retry(a, lane, sr.row);
-            delta = 0.f;  // k_split_resid leaves the row's residuals alone
-        } else if (sub == 0) {
-            a.X[(int64_t)sr.row * a.d + a.p0 + col] -= delta;
+            for (int j = 0; j < B; ++j) acc[j] = red[col * B + j];
+            float g = red[B * B + col];
+            const float lam = a.lambda * (1.0f + a.nu * (float)sr.len);
+#pragma unroll
+            for (int j = 0; j < B; ++j)
+                acc[j] += a.alpha0 * a.G[(int64_t)(a.p0 + j) * B + col] + (j == col ? lam : 0.f);
+            g += a.R[(int64_t)sr.row * B + col];
+            float delta = 0.f;
+            const bool ok = chol_solve<B>(acc, g, col, sub, w, a.force_fp64 != 0, delta);
+            if (!ok) {
+                queue_retry(a, lane, sr.row);
+                delta = 0.f;  // k_split_resid leaves the row's residuals alone
+            } else if (sub == 0) {
+                a.X[(int64_t)sr.row * a.d + a.p0 + col] -= delta;
+            }
+            if (sub == 0) a.delta[(int64_t)i * B + col] = delta;
         }
-        if (sub == 0) a.delta[(int64_t)i * B + col] = delta;
+        __syncthreads();
     }
+}
+
+template <int B>
+constexpr int split_solve_smem() {
+    return ((B * B + B + 3) / 4 * 4 + (B + 3) / 4 * 4 + B * (B + 1)) * 4;
 }
 
 // One warp per chunk of a split row: e_s -= <delta_row, f_{c_s,pi}>.
@@ -739,8 +751,8 @@ cudaError_t launch_step_b(const StepArgs &a, cudaStream_t s) {
     static int per_sm = 0;
     if (!attr_done) {
         cudaError_t e1 = cudaFuncSetAttribute(kmain, cudaFuncAttributeMaxDynamicSharedMemorySize, MAIN_SMEM);
-        cudaError_t e2 = cudaFuncSetAttribute(k_split_solve<B>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+        cudaError_t e2 = cudaFuncSetAttribute(k_split_solve<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              split_solve_smem<B>());
         cudaError_t e3 = cudaFuncSetAttribute(k_split_resid<B, PERM>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
         if (e1 != cudaSuccess) return e1;
@@ -761,9 +773,9 @@ cudaError_t launch_step_b(const StepArgs &a, cudaStream_t s) {
         prof_mark(a.prof, -1, s);
     }
     if (a.n_split > 0) {
-        const int g2 = (a.n_split + C::WARPS - 1) / C::WARPS;
+        const int g2 = a.n_split < 152 * 8 ? a.n_split : 152 * 8;
         prof_mark(a.prof, K_SPLIT_SOLVE, s);
-        k_split_solve<B><<<g2, C::WARPS * 32, C::SMEM_BYTES, s>>>(a);
+        k_split_solve<B><<<g2, 256, split_solve_smem<B>(), s>>>(a);
         prof_mark(a.prof, -1, s);
     }
     return cudaGetLastError();
