@@ -163,6 +163,8 @@ struct HostTasks {
     int32_t n_slots = 0;
 };
 
+constexpr int64_t kResidPiece = 128;  // interactions per residual-update piece of a split row
+
 HostTasks build_tasks(const std::vector<int64_t> &ptr, int32_t n_rows, int64_t split_len) {
     HostTasks ht;
     ht.tasks.reserve(n_rows);
@@ -182,8 +184,12 @@ HostTasks build_tasks(const std::vector<int64_t> &ptr, int32_t n_rows, int64_t s
             const int64_t len = std::min(chunk, n - b);
             Task t{ptr[r] + b, (int32_t)len, r, slot0 + ns, srow};
             ht.tasks.push_back(t);
-            ht.stasks.push_back(t);
             ++ns;
+        }
+        // residual-update pieces of the row (any cut works: no reduction)
+        for (int64_t b = 0; b < n; b += kResidPiece) {
+            const int64_t len = std::min<int64_t>(kResidPiece, n - b);
+            ht.stasks.push_back({ptr[r] + b, (int32_t)len, r, -1, srow});
         }
         ht.split.push_back({ptr[r], (int32_t)n, r, slot0, ns});
         ht.n_slots += ns;

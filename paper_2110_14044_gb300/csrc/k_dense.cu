@@ -21,24 +21,26 @@ __device__ __forceinline__ float dot4(float4 a, float4 b) {
 }
 
 // ------------------------------------------------------------------ residual
-// One warp per user row.  The warp is split into sub-groups of SG lanes; each
-// sub-group handles one interaction at a time, lane l of the sub-group owning
-// float4 chunks l, l + SG, ... (MAXV of them) of the d-vector.  Each sub-group
-// keeps two interactions in flight (independent gathers) per iteration.
+// One warp per user row.  The warp loads the column ids of 32 interactions at
+// once (one coalesced load), then sub-groups of SG = 2^SGL lanes take
+// interactions sub, sub + 32/SG, ...; lane l of a sub-group owns float4 chunks
+// l, l + SG, ... (MAXV of them) of the d-vector.  Each sub-group keeps up to
+// four gathers in flight before it reduces.
 // LOSS = false: write e[s] = <w_u, h_i> - y_s.
 // LOSS = true : accumulate alpha_s (<w_u, h_i> - y_s)^2 in FP64, one partial per block.
-template <int MAXV, bool LOSS>
+template <int SGL, int MAXV, bool LOSS>
 __global__ void __launch_bounds__(256) k_residual(const int64_t *__restrict__ u_ptr,
                                                   const int32_t *__restrict__ u_idx,
                                                   const float *__restrict__ W,
                                                   const float *__restrict__ H,
                                                   const float *__restrict__ y,
                                                   const float *__restrict__ alpha,
-                                                  int32_t n_users, int32_t d, int sg_log,
+                                                  int32_t n_users, int32_t d,
                                                   float *__restrict__ e, double *__restrict__ part) {
+    constexpr int SG = 1 << SGL, NSUB = 32 / SG;  // NSUB sub-groups, SG interactions each per chunk
+    constexpr int U = SG < 4 ? SG : 4;
     const int lane = threadIdx.x & 31;
-    const int SG = 1 << sg_log;
-    const int sub = lane >> sg_log, sl = lane & (SG - 1), nsub = 32 >> sg_log;
+    const int sub = lane >> SGL, sl = lane & (SG - 1);
     const int nv4 = d >> 2;
     const float4 *W4 = reinterpret_cast<const float4 *>(W);
     const float4 *H4 = reinterpret_cast<const float4 *>(H);
@@ -52,37 +54,43 @@ __global__ void __launch_bounds__(256) k_residual(const int64_t *__restrict__ u_
             wv[m] = v < nv4 ? W4[(int64_t)u * nv4 + v] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const int64_t beg = u_ptr[u], end = u_ptr[u + 1];
-        for (int64_t s0 = beg; s0 < end; s0 += 2 * nsub) {
-            const int64_t s1 = s0 + sub, s2 = s0 + nsub + sub;
-            const bool v1 = s1 < end, v2 = s2 < end;
-            const int64_t c1 = v1 ? u_idx[s1] : 0, c2 = v2 ? u_idx[s2] : 0;
-            float a1 = 0.f, a2 = 0.f;
-            float4 h1[MAXV], h2[MAXV];
+        for (int64_t s0 = beg; s0 < end; s0 += 32) {
+            const int cnt = (int)min((int64_t)32, end - s0);
+            const int my_c = lane < cnt ? u_idx[s0 + lane] : 0;
 #pragma unroll
-            for (int m = 0; m < MAXV; ++m) {
-                const int v = sl + m * SG;
-                h1[m] = (v1 && v < nv4) ? __ldg(H4 + c1 * nv4 + v) : make_float4(0.f, 0.f, 0.f, 0.f);
-                h2[m] = (v2 && v < nv4) ? __ldg(H4 + c2 * nv4 + v) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+            for (int m0 = 0; m0 < SG; m0 += U) {
+                float acc[U];
+                float4 h[U][MAXV];
 #pragma unroll
-            for (int m = 0; m < MAXV; ++m) {
-                a1 += dot4(wv[m], h1[m]);
-                a2 += dot4(wv[m], h2[m]);
-            }
-            for (int o = SG >> 1; o > 0; o >>= 1) {
-                a1 += __shfl_xor_sync(kFull, a1, o);
-                a2 += __shfl_xor_sync(kFull, a2, o);
-            }
-            if (sl == 0) {
-                if (v1) {
-                    const float r = a1 - (y ? y[s1] : 1.0f);
-                    if (LOSS) loss += (alpha ? (double)alpha[s1] : 1.0) * (double)r * (double)r;
-                    else e[s1] = r;
+                for (int q = 0; q < U; ++q) {
+                    const int k = sub + NSUB * (m0 + q);
+                    const int64_t c = __shfl_sync(kFull, my_c, k);
+                    acc[q] = 0.f;
+#pragma unroll
+                    for (int m = 0; m < MAXV; ++m) {
+                        const int v = sl + m * SG;
+                        h[q][m] = (k < cnt && v < nv4) ? __ldg(H4 + c * nv4 + v)
+                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
                 }
-                if (v2) {
-                    const float r = a2 - (y ? y[s2] : 1.0f);
-                    if (LOSS) loss += (alpha ? (double)alpha[s2] : 1.0) * (double)r * (double)r;
-                    else e[s2] = r;
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+#pragma unroll
+                    for (int m = 0; m < MAXV; ++m) acc[q] += dot4(wv[m], h[q][m]);
+#pragma unroll
+                    for (int o = SG >> 1; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(kFull, acc[q], o);
+                }
+                if (sl == 0) {
+#pragma unroll
+                    for (int q = 0; q < U; ++q) {
+                        const int k = sub + NSUB * (m0 + q);
+                        if (k < cnt) {
+                            const int64_t s = s0 + k;
+                            const float r = acc[q] - (y ? y[s] : 1.0f);
+                            if (LOSS) loss += (alpha ? (double)alpha[s] : 1.0) * (double)r * (double)r;
+                            else e[s] = r;
+                        }
+                    }
                 }
             }
         }
@@ -364,15 +372,23 @@ cudaError_t launch_residual_impl(const int64_t *u_ptr, const int32_t *u_idx, con
     while ((2 << sg_log) <= 32 && (2 << sg_log) * 4 <= nv4) ++sg_log;
     const int SG = 1 << sg_log;
     const int maxv = (nv4 + SG - 1) / SG;
-#define IALS_RES(MV)                                                                         \
-    k_residual<MV, LOSS><<<grid, 256, 0, s>>>(u_ptr, u_idx, W, H, y, alpha, n_users, d,      \
-                                              sg_log, e, part)
-    if (maxv <= 1) IALS_RES(1);
-    else if (maxv <= 2) IALS_RES(2);
-    else if (maxv <= 4) IALS_RES(4);
-    else if (maxv <= 8) IALS_RES(8);
-    else if (maxv <= 16) IALS_RES(16);
-    else if (maxv <= 32) IALS_RES(32);
+#define IALS_RES(SGL, MV)                                                                    \
+    k_residual<SGL, MV, LOSS><<<grid, 256, 0, s>>>(u_ptr, u_idx, W, H, y, alpha, n_users, d, \
+                                                   e, part)
+    // maxv < 8 whenever sg_log < 5 (the loop above stops at 4 chunks per lane)
+    if (sg_log == 0) {
+        if (maxv <= 1) IALS_RES(0, 1);
+        else if (maxv <= 2) IALS_RES(0, 2);
+        else if (maxv <= 4) IALS_RES(0, 4);
+        else IALS_RES(0, 8);
+    } else if (sg_log == 1) { if (maxv <= 4) IALS_RES(1, 4); else IALS_RES(1, 8); }
+    else if (sg_log == 2) { if (maxv <= 4) IALS_RES(2, 4); else IALS_RES(2, 8); }
+    else if (sg_log == 3) { if (maxv <= 4) IALS_RES(3, 4); else IALS_RES(3, 8); }
+    else if (sg_log == 4) { if (maxv <= 4) IALS_RES(4, 4); else IALS_RES(4, 8); }
+    else if (maxv <= 4) IALS_RES(5, 4);
+    else if (maxv <= 8) IALS_RES(5, 8);
+    else if (maxv <= 16) IALS_RES(5, 16);
+    else if (maxv <= 32) IALS_RES(5, 32);
     else return cudaErrorInvalidValue;
 #undef IALS_RES
     return cudaGetLastError();

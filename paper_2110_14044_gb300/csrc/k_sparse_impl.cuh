@@ -118,10 +118,15 @@ __device__ __forceinline__ void stage_chunk(const StepArgs &a, int64_t begin, in
     __syncwarp();
 }
 
-// Warp Cholesky solve A delta = g.  Lane l holds row/column col = l % B of the
-// symmetric matrix in A[] and entry col of g.  Returns false (warp-uniform) if
-// a pivot is not positive, not finite, or has lost all but ~17 bits relative to
-// the original diagonal.  On success `delta` holds entry col of the solution.
+// Warp Cholesky solve A delta = g.  Lane l holds row col = l % B of the
+// symmetric matrix in A[] (entries right of the diagonal may hold anything
+// finite) and entry col of g.  Right-looking factorisation, one column per
+// step: the pivot is broadcast with a shuffle and column k of L is exchanged
+// through a double-buffered column in w.L, so each step needs one __syncwarp.
+// Lane k checks its own pivot (positive, finite, and not below 1e-5 of its
+// original diagonal, i.e. no more than ~17 bits lost); one vote at the end
+// decides for the whole warp.  Returns false (warp-uniform) on a bad pivot or a
+// non-finite solution; on success `delta` holds entry col of the solution.
 template <int B>
 __device__ __forceinline__ bool chol_solve(float (&A)[B], float g, int col, int sub,
                                            const WarpSmem &w, bool force_fail, float &delta) {
@@ -129,25 +134,24 @@ __device__ __forceinline__ bool chol_solve(float (&A)[B], float g, int col, int 
 #pragma unroll
     for (int j = 0; j < B; ++j)
         if (j == col) diag0 = A[j];
-    bool ok = !force_fail;
+    bool bad = force_fail;
     float inv_diag = 0.f;
+    float *cb = w.L;  // two column buffers of B floats while factorising
 #pragma unroll
     for (int k = 0; k < B; ++k) {
+        if (col == k) bad = bad || !(A[k] > 1e-5f * diag0) || !(A[k] <= 3.0e38f);
         const float akk = __shfl_sync(kFull, A[k], k);
-        const float d0 = __shfl_sync(kFull, diag0, k);
-        ok = ok && (akk > 1e-5f * d0) && (akk <= 3.0e38f);
-        const float lkk = sqrtf(fmaxf(akk, 1e-30f));
-        const float inv = 1.0f / lkk;
+        const float inv = rsqrtf(fmaxf(akk, 1e-30f));
         const float lck = A[k] * inv;
         if (col == k) inv_diag = inv;
         A[k] = lck;
-        __syncwarp();
-        if (sub == 0) w.v[col] = lck;
+        float *v = cb + (k & 1) * B;
+        if (sub == 0) v[col] = lck;
         __syncwarp();
 #pragma unroll
-        for (int j = k + 1; j < B; ++j) A[j] -= lck * w.v[j];
+        for (int j = k + 1; j < B; ++j) A[j] -= lck * v[j];
     }
-    if (!ok) return false;
+    if (__any_sync(kFull, bad)) return false;
     // forward: L z = g
     float z = g;
 #pragma unroll
@@ -172,7 +176,7 @@ __device__ __forceinline__ bool chol_solve(float (&A)[B], float g, int col, int 
         else if (col == k) x = xk;
     }
     delta = x;
-    return isfinite(x);
+    return __all_sync(kFull, isfinite(x));
 }
 
 template <int B>
@@ -629,6 +633,59 @@ __global__ void __launch_bounds__(256) k_split_resid(const StepArgs a, const Tas
     }
 }
 
+// One warp per piece (<= 128 interactions) of a split row: e_s -= <delta_row,
+// f_{c_s,pi}>, with the slices gathered by cp.async into two staging buffers
+// and the column ids / residual positions loaded one chunk ahead.
+template <int B, bool PERM>
+__global__ void __launch_bounds__(256) k_split_resid_tiled(const StepArgs a) {
+    using C = TileCfg<B>;
+    constexpr int SB = C::SB, CH = C::CH;
+    extern __shared__ float4 smem4[];
+    float *smem = reinterpret_cast<float *>(smem4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *wbase = smem + warp * (2 * C::BUF + C::VEC);
+    float *vv = wbase + 2 * C::BUF;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.n_stasks; t += nw) {
+        const Task tk = a.stasks[t];
+        __syncwarp();
+        if (lane < B) vv[lane] = a.delta[(int64_t)tk.srow * B + lane];
+        const int nch = (tk.len + CH - 1) / CH;
+        int cB = 0;
+        int64_t qB = 0;
+        auto meta = [&](int j) {
+            const int cnt = min(CH, tk.len - j * CH);
+            if (lane < cnt) {
+                const int64_t s = tk.begin + (int64_t)j * CH + lane;
+                cB = a.idx[s];
+                qB = PERM ? (int64_t)a.pos[s] : s;
+            }
+        };
+        meta(0);
+        int64_t qc = qB;
+        gather_async<B>(wbase, a.F, a.d, a.p0, cB, min(CH, tk.len), lane);
+        cp_async_commit();
+        if (nch > 1) meta(1);
+        for (int ch = 0; ch < nch; ++ch) {
+            const int bi = ch & 1;
+            cp_async_wait_all();
+            __syncwarp();
+            int64_t qn = 0;
+            if (ch + 1 < nch) {
+                gather_async<B>(wbase + (bi ^ 1) * C::BUF, a.F, a.d, a.p0, cB,
+                                min(CH, tk.len - (ch + 1) * CH), lane);
+                cp_async_commit();
+                qn = qB;
+                if (ch + 2 < nch) meta(ch + 2);
+            }
+            const int cnt = min(CH, tk.len - ch * CH);
+            if (lane < cnt) a.e[qc] -= dot_slice<B>(vv, wbase + bi * C::BUF + lane * SB);
+            __syncwarp();
+            qc = qn;
+        }
+    }
+}
+
 // FP64 re-solve of queued rows: statistics accumulated from scratch in FP64
 // (the FP32 row term R_r is reused), Cholesky in FP64.  A row that still has
 // a pivot that is not positive, or below 1e-13 of its original diagonal (the
@@ -753,8 +810,15 @@ cudaError_t launch_step_b(const StepArgs &a, cudaStream_t s) {
         cudaError_t e1 = cudaFuncSetAttribute(kmain, cudaFuncAttributeMaxDynamicSharedMemorySize, MAIN_SMEM);
         cudaError_t e2 = cudaFuncSetAttribute(k_split_solve<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               split_solve_smem<B>());
-        cudaError_t e3 = cudaFuncSetAttribute(k_split_resid<B, PERM>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+        cudaError_t e3;
+        if constexpr (B >= 8) {
+            constexpr int RS = 8 * (2 * TileCfg<(B >= 8 ? B : 8)>::BUF + TileCfg<(B >= 8 ? B : 8)>::VEC) * 4;
+            e3 = cudaFuncSetAttribute(k_split_resid_tiled<B, PERM>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, RS);
+        } else {
+            e3 = cudaFuncSetAttribute(k_split_resid<B, PERM>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+        }
         if (e1 != cudaSuccess) return e1;
         if (e2 != cudaSuccess) return e2;
         if (e3 != cudaSuccess) return e3;
@@ -786,9 +850,14 @@ cudaError_t launch_split_resid_b(const StepArgs &a, cudaStream_t s) {
     using C = SparseCfg<B>;
     if (a.n_stasks > 0) {
         int g3 = (a.n_stasks + C::WARPS - 1) / C::WARPS;
-        if (g3 > 152 * 4) g3 = 152 * 4;
+        if (g3 > 152 * 8) g3 = 152 * 8;
         prof_mark(a.prof, K_SPLIT_RESID, s);
-        k_split_resid<B, PERM><<<g3, C::WARPS * 32, C::SMEM_BYTES, s>>>(a, a.stasks, a.n_stasks);
+        if constexpr (B >= 8) {
+            constexpr int RS = 8 * (2 * TileCfg<(B >= 8 ? B : 8)>::BUF + TileCfg<(B >= 8 ? B : 8)>::VEC) * 4;
+            k_split_resid_tiled<B, PERM><<<g3, 256, RS, s>>>(a);
+        } else {
+            k_split_resid<B, PERM><<<g3, C::WARPS * 32, C::SMEM_BYTES, s>>>(a, a.stasks, a.n_stasks);
+        }
         prof_mark(a.prof, -1, s);
     }
     prof_mark(a.prof, K_RETRY, s);

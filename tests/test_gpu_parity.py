@@ -334,3 +334,19 @@ def test_set_factors_refreshes_residual_cache():
     e = m.residuals()
     P = oracle.Problem.from_data(prob.data, 16, 8, 0.1, 1e-3)
     np.testing.assert_allclose(e, oracle.predict(P, prob.W0, prob.H0) - 1.0, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("d,b", [(4, 4), (20, 4), (48, 16), (100, 4), (1024, 32)])
+def test_unusual_dimensions(d, b):
+    prob = small(d=d, seed=16)
+    m = Model(prob.data, d, b, 0.1, 1e-3, 0.3, W0=prob.W0, H0=prob.H0)
+    P = oracle.Problem.from_data(prob.data, d, b, 0.1, 1e-3, 0.3)
+    np.testing.assert_allclose(m.residuals(), oracle.predict(P, prob.W0, prob.H0) - 1.0,
+                               rtol=1e-5, atol=1e-6)
+    W, H = P.factors(prob.W0, prob.H0)
+    yhat = oracle.predict(P, W, H)
+    for side in (0, 1):
+        assert m.block_step(side, d // b - 1) == 0
+        oracle.halfstep(P, side, d // b - 1, W, H, yhat)
+    Wg, Hg = m.factors()
+    assert rel_embed_err(Wg, W) <= STEP_TOL and rel_embed_err(Hg, H) <= STEP_TOL
