@@ -171,6 +171,27 @@ ials_status ials_work_model(ials_ctx *ctx, double *bytes, double *flops, int32_t
 ials_status ials_partial_gramian(const float *X, int64_t n, int32_t d, int32_t p0, int32_t bs,
                                  float *G, void *cuda_stream);
 
+/* The same partial Gramian for callers that cannot allocate device memory:
+ * code whose device memory belongs to another allocator (a framework's caching
+ * allocator, a fixed arena) or a latency-bound loop in which cudaMalloc /
+ * cudaFree, which may synchronise the device, are not acceptable.  The paper
+ * has no counterpart; this is a library convenience.
+ * The split-K partial sums live in one fixed device array of 2^21 floats
+ * (8 MiB) that every GPU loading the library holds until the process exits;
+ * calls with d * bs > 2^21 fail with IALS_EINVAL.  X (n x d) and G (d x bs)
+ * are caller-owned device arrays.  Nothing is allocated or freed: no
+ * cudaMalloc, cudaFree or allocating library routine is called.
+ * The call only enqueues work on cuda_stream and returns; G is ready when the
+ * stream reaches that point.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents: calls that overlap on the GPU (another
+ * stream, another thread) race on it and give wrong results, so serialise
+ * them.  Every partial slot is written before it is read, so no clearing is
+ * needed between calls. */
+ials_status ials_partial_gramian_noalloc(const float *X, int64_t n, int32_t d, int32_t p0,
+                                         int32_t bs, float *G, void *cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *ials_last_error(void);
 

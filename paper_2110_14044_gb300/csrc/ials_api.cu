@@ -36,6 +36,14 @@ ials_status fail(ials_status st, const std::string &msg) {
     return st;
 }
 
+}  // namespace
+
+namespace ials {
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace ials
+
+namespace {
+
 ials_status cuda_fail(cudaError_t e, const char *what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
     cudaGetLastError();  // do not leak a non-sticky error into the next call

@@ -112,6 +112,12 @@ cudaError_t launch_frobenius(const double *A, const double *B, int32_t n, double
 int64_t gram_ws_floats(int64_t n, int32_t d, int32_t bs);
 cudaError_t launch_gram(const float *X, int64_t n, int32_t d, int32_t p0, int32_t bs, float *G,
                         float *ws, cudaStream_t s);
+// The same split-K Gramian with a caller-provided workspace of max_floats
+// floats: the row ranges are lengthened until the partials fit.
+// gram_ws_floats_capped returns the floats used, or -1 if d * bs > max_floats.
+int64_t gram_ws_floats_capped(int64_t n, int32_t d, int32_t bs, int64_t max_floats);
+cudaError_t launch_gram_capped(const float *X, int64_t n, int32_t d, int32_t p0, int32_t bs,
+                               float *G, float *ws, int64_t max_floats, cudaStream_t s);
 // Full FP64-accumulated Gramian G64 = X^T X (d x d); ws holds gram64_ws_doubles(n, d).
 int64_t gram64_ws_doubles(int64_t n, int32_t d);
 cudaError_t launch_gram64(const float *X, int64_t n, int32_t d, double *G64, double *ws,

@@ -448,6 +448,32 @@ cudaError_t launch_gram(const float *X, int64_t n, int32_t d, int32_t p0, int32_
     return cudaGetLastError();
 }
 
+int64_t gram_ws_floats_capped(int64_t n, int32_t d, int32_t bs, int64_t max_floats) {
+    GramPlan p = gram_plan(n, d, bs);
+    const int64_t per_split = (int64_t)d * bs;
+    if (per_split > max_floats) return -1;
+    if ((int64_t)p.nsplit * per_split > max_floats) p.nsplit = (int)(max_floats / per_split);
+    return (int64_t)p.nsplit * per_split;
+}
+
+cudaError_t launch_gram_capped(const float *X, int64_t n, int32_t d, int32_t p0, int32_t bs,
+                               float *G, float *ws, int64_t max_floats, cudaStream_t s) {
+    const int64_t count = (int64_t)d * bs;
+    if (count > max_floats) return cudaErrorInvalidValue;
+    if (n == 0) return cudaMemsetAsync(G, 0, sizeof(float) * count, s);
+    GramPlan p = gram_plan(n, d, bs);
+    if ((int64_t)p.nsplit * count > max_floats) {
+        // fewer, longer row ranges so that the partials fit the given workspace
+        const int64_t ns = max_floats / count;
+        const int64_t kblocks = (n + GK - 1) / GK;
+        p.rows_per = (kblocks + ns - 1) / ns * GK;
+        p.nsplit = (int)((n + p.rows_per - 1) / p.rows_per);
+    }
+    launch_gram_tiles<false>(p, X, n, d, p0, bs, ws, s);
+    k_gram_reduce<float><<<(unsigned)((count + 255) / 256), 256, 0, s>>>(ws, p.nsplit, count, G);
+    return cudaGetLastError();
+}
+
 int64_t gram64_ws_doubles(int64_t n, int32_t d) {
     GramPlan p = gram_plan(n, d, d);
     return (int64_t)p.nsplit * d * d;
