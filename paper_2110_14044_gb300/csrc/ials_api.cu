@@ -101,7 +101,9 @@ struct SideDev {
     int32_t n_slots = 0;
 };
 
-bool is_pow2_le32(int b) { return b == 1 || b == 2 || b == 4 || b == 8 || b == 16 || b == 32; }
+bool valid_block(int b) {
+    return b == 1 || b == 2 || b == 4 || b == 8 || b == 16 || b == 32 || b == 64 || b == 128;
+}
 
 cudaError_t launch_sparse(const StepArgs &a, cudaStream_t s) {
     switch (a.b) {
@@ -111,6 +113,8 @@ cudaError_t launch_sparse(const StepArgs &a, cudaStream_t s) {
         case 8: return launch_sparse_b8(a, s);
         case 16: return launch_sparse_b16(a, s);
         case 32: return launch_sparse_b32(a, s);
+        case 64: return launch_sparse_b64(a, s);
+        case 128: return launch_sparse_b128(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -331,8 +335,8 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     *out = nullptr;
     const ials_params p = *params;
     if (p.d < 4 || p.d > 4096 || p.d % 4 != 0) return fail(IALS_EINVAL, "d must be a multiple of 4 in [4, 4096]");
-    if (!is_pow2_le32(p.b) || p.d % p.b != 0)
-        return fail(IALS_EINVAL, "b must be a power of two <= 32 that divides d");
+    if (!valid_block(p.b) || p.d % p.b != 0)
+        return fail(IALS_EINVAL, "b must be a power of two <= 128 that divides d");
     if (!(p.alpha0 >= 0) || !(p.lambda >= 0) || !(p.nu >= 0) || !std::isfinite(p.alpha0) ||
         !std::isfinite(p.lambda) || !std::isfinite(p.nu))
         return fail(IALS_EINVAL, "alpha0, lambda, nu must be finite and >= 0");

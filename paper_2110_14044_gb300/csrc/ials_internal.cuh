@@ -138,5 +138,8 @@ cudaError_t launch_sparse_b4(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_sparse_b8(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_sparse_b16(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_sparse_b32(const StepArgs &a, cudaStream_t s);
+// block sizes 64 and 128 (k_sparse_b64.cu, k_sparse_b128.cu): one CTA per task
+cudaError_t launch_sparse_b64(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_sparse_b128(const StepArgs &a, cudaStream_t s);
 
 }  // namespace ials

@@ -1,0 +1,541 @@
+// Sparse block step of Algorithm 3 for block sizes B = 64 and 128 (one CTA per task).
+//
+// The step is the one of k_sparse_impl.cuh (Eqs. 11-12, Newton solve, apply,
+// residual update); only the work layout changes because the b x b statistics
+// no longer fit a warp's registers:
+//  * accumulation: A_r is cut into 8 x 8 tiles; the NTL = (B/8)(B/8+1)/2 tiles
+//    on or below the diagonal are owned by NTL threads of each of NG
+//    interaction groups (group g takes staged interactions g, g + NG, ...).
+//    Slices are gathered with cp.async into two staging buffers.  Group
+//    partials are summed in group order into a shared (B+1) x (B+4) matrix M
+//    whose last row holds the gradient.
+//  * solve: a blocked right-looking Cholesky of M in shared memory with panel
+//    width 8 (diagonal block by one warp, panel by one thread per row, trailing
+//    update by 2 x 8 output units).  Row B rides along, so the forward
+//    substitution L z = g falls out of the factorisation; the backward
+//    substitution runs panel by panel from the bottom.
+//  * the same routine, templated on double, is the FP64 retry.
+#pragma once
+
+#include "k_sparse_impl.cuh"
+
+namespace ials {
+
+template <int B>
+struct CtaCfg {
+    static constexpr int NB = B / 8;
+    static constexpr int NTL = NB * (NB + 1) / 2;
+    static constexpr int NG = B == 64 ? 7 : 2;
+    static constexpr int ACTIVE = NTL * NG;
+    static constexpr int THREADS = (ACTIVE + 31) / 32 * 32;
+    static constexpr int SB = B + 4;   // row stride of staging buffers and of M
+    static constexpr int CH = 32;
+    static constexpr int BUF = CH * SB;
+    // floats: two staging buffers, e[2][CH], a[2][CH], M (B+1 rows), diag0, invd, x, flag
+    static constexpr int SMEM_FLOATS = 2 * BUF + 4 * CH + (B + 1) * SB + 3 * B + 4;
+    static constexpr int SMEM_BYTES = SMEM_FLOATS * 4;
+};
+
+// Lower-triangle tile index t -> (ti, tj), ti >= tj.
+__device__ __forceinline__ void tri_index(int t, int &ti, int &tj) {
+    int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    while (i * (i + 1) / 2 > t) --i;
+    ti = i;
+    tj = t - i * (i + 1) / 2;
+}
+
+// Blocked Cholesky of the SPD matrix in rows 0..B-1 of M (lower part used),
+// carrying the right-hand side in row B.  On return the lower part of rows
+// 0..B-1 holds L, row B holds z = L^{-1} rhs, invd[k] = 1 / L_kk.  A pivot that
+// is not above rel * diag0[k] (or not finite) sets *bad.  All threads call it.
+template <int B, int SM, typename T>
+__device__ void cta_cholesky(T *M, T *invd, const T *diag0, int *bad, T rel) {
+    constexpr int NB = B / 8;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int p = 0; p < NB; ++p) {
+        const int k0 = 8 * p;
+        if (tid < 32) {  // diagonal 8 x 8 block: lane r < 8 owns row k0 + r
+            const int lane = tid;
+            T r[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) r[j] = lane < 8 ? M[(k0 + lane) * SM + k0 + j] : T(0);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const T akk = __shfl_sync(kFull, r[k], k);
+                if (lane == k && (!(akk > rel * diag0[k0 + k]) || !(akk < T(1e300)))) *bad = 1;
+                const T l = sqrt(akk > T(0) ? akk : T(1e-30));
+                const T inv = T(1) / l;
+                const T lck = r[k] * inv;
+                if (lane == k) invd[k0 + k] = inv;
+                r[k] = lck;
+#pragma unroll
+                for (int j = k + 1; j < 8; ++j) r[j] -= lck * __shfl_sync(kFull, lck, j);
+            }
+            if (lane < 8) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j <= lane) M[(k0 + lane) * SM + k0 + j] = r[j];
+            }
+        }
+        __syncthreads();
+        // panel: rows k0+8 .. B (the last one is the right-hand side): x L_D^T = a
+        for (int i = k0 + 8 + tid; i <= B; i += nt) {
+            T x[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[j] = M[i * SM + k0 + j];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+#pragma unroll
+                for (int m = 0; m < j; ++m) x[j] -= x[m] * M[(k0 + j) * SM + k0 + m];
+                x[j] *= invd[k0 + j];
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) M[i * SM + k0 + j] = x[j];
+        }
+        __syncthreads();
+        // trailing update: rows i in [k0+8, B], columns j in [k0+8, min(i, B-1)], in units
+        // of 2 rows x 8 columns: M[i][j] -= sum_m M[i][k0+m] M[j][k0+m]
+        const int r0 = k0 + 8;
+        const int nrow = B + 1 - r0;            // includes the right-hand side row
+        const int nrp = (nrow + 1) / 2;         // row pairs
+        const int ncb = (B - r0) / 8;           // column blocks
+        const int units = nrp * ncb;
+        for (int u = tid; u < units; u += nt) {
+            const int rp = u / ncb, cb = u % ncb;
+            const int i0 = r0 + 2 * rp, j0 = r0 + 8 * cb;
+            if (j0 > i0 + 1 && i0 < B) continue;  // wholly above the diagonal (the rhs row never is)
+            T a0[8], a1[8];
+            const bool two = i0 + 1 <= B;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                a0[m] = M[i0 * SM + k0 + m];
+                a1[m] = two ? M[(i0 + 1) * SM + k0 + m] : T(0);
+            }
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const int j = j0 + jj;
+                T t0 = 0, t1 = 0;
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const T bm = M[j * SM + k0 + m];
+                    t0 += a0[m] * bm;
+                    t1 += a1[m] * bm;
+                }
+                if (j <= i0 || i0 == B) M[i0 * SM + j] -= t0;
+                if (two && (j <= i0 + 1 || i0 + 1 == B)) M[(i0 + 1) * SM + j] -= t1;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Backward substitution L^T x = z (z in x on entry), panel by panel from the bottom.
+template <int B, int SM, typename T>
+__device__ void cta_backsolve(const T *M, const T *invd, T *x) {
+    constexpr int NB = B / 8;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int p = NB - 1; p >= 0; --p) {
+        const int k0 = 8 * p;
+        if (tid == 0) {
+            for (int j = 7; j >= 0; --j) {
+                T v = x[k0 + j];
+                for (int m = j + 1; m < 8; ++m) v -= M[(k0 + m) * SM + k0 + j] * x[k0 + m];
+                x[k0 + j] = v * invd[k0 + j];
+            }
+        }
+        __syncthreads();
+        for (int j = tid; j < k0; j += nt) {
+            T v = x[j];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v -= M[(k0 + m) * SM + j] * x[k0 + m];
+            x[j] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// Adds alpha0 G_pipi + lambda I to rows 0..B-1 of M (lower part) and R_r to row B;
+// records the diagonal in diag0.
+template <int B, int SM, typename T>
+__device__ void cta_dense_terms(const StepArgs &a, T *M, T *diag0, int row, T lam) {
+    for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+        const int i = e / B, j = e % B;
+        if (j > i) continue;
+        T v = M[i * SM + j] + (T)a.alpha0 * (T)a.G[(int64_t)(a.p0 + i) * B + j];
+        if (i == j) {
+            v += lam;
+            diag0[i] = v;
+        }
+        M[i * SM + j] = v;
+    }
+    for (int j = threadIdx.x; j < B; j += blockDim.x) M[B * SM + j] += (T)a.R[(int64_t)row * B + j];
+}
+
+// Gather `cnt` slices starting at CSR position s0 into buf (all threads).
+template <int B>
+__device__ __forceinline__ void cta_gather(const StepArgs &a, int64_t s0, int cnt, float *buf) {
+    constexpr int V = B / 4, SB = CtaCfg<B>::SB;
+    for (int f = threadIdx.x; f < cnt * V; f += blockDim.x) {
+        const int k = f / V, v = f % V;
+        const int64_t c = a.idx[s0 + k];
+        cp_async16(buf + k * SB + 4 * v, a.F + c * a.d + a.p0 + 4 * v);
+    }
+}
+
+// Residual update e_s -= <x, f_{c_s,pi}> for the CSR range [s0, s0 + len):
+// slices staged 32 at a time, one warp per interaction with lanes splitting b.
+template <int B, bool PERM>
+__device__ void cta_residual_update(const StepArgs &a, int64_t s0, int len, const float *x,
+                                    float *buf) {
+    constexpr int CH = CtaCfg<B>::CH, SB = CtaCfg<B>::SB;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c0 = 0; c0 < len; c0 += CH) {
+        const int cnt = min(CH, len - c0);
+        cta_gather<B>(a, s0 + c0, cnt, buf);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+        for (int k = warp; k < cnt; k += nw) {
+            float t = 0.f;
+#pragma unroll
+            for (int j = lane; j < B; j += 32) t += x[j] * buf[k * SB + j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+            if (lane == 0) {
+                const int64_t s = s0 + c0 + k;
+                const int64_t q = PERM ? (int64_t)a.pos[s] : s;
+                a.e[q] -= t;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int B, bool PERM, bool HAS_A>
+__global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_sparse_cta(const StepArgs a) {
+    using C = CtaCfg<B>;
+    constexpr int SB = C::SB, CH = C::CH;
+    extern __shared__ float4 smem4[];
+    float *smem = reinterpret_cast<float *>(smem4);
+    float *buf0 = smem;                      // staging buffer bi at buf0 + bi * BUF
+    float *she = smem + 2 * C::BUF;          // residuals (weighted) [2][CH]
+    float *sha = she + 2 * CH;               // weights [2][CH]
+    float *M = sha + 2 * CH;                 // (B+1) x SB
+    float *diag0 = M + (B + 1) * SB;
+    float *invd = diag0 + B;
+    float *xv = invd + B;
+    int *flag = reinterpret_cast<int *>(xv + B);  // [0] task, [1] bad
+    const int tid = threadIdx.x;
+    const bool active = tid < C::ACTIVE;
+    const int grp = active ? tid / C::NTL : C::NG;
+    const int kstart = active ? grp : C::CH;  // idle threads skip the accumulation
+    int ti = 0, tj = 0;
+    tri_index(tid % C::NTL, ti, tj);
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) flag[0] = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int tsk = flag[0];
+        if (tsk >= a.n_tasks) break;
+        const Task tk = a.tasks[tsk];
+        const int nch = (tk.len + CH - 1) / CH;
+        float acc[8][8], gacc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            gacc[i] = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        }
+        auto meta = [&](int j, int bi) {  // residual and weight of chunk j into buffer bi (warp 0)
+            const int cnt = min(CH, tk.len - j * CH);
+            if (tid < cnt) {
+                const int64_t s = tk.begin + (int64_t)j * CH + tid;
+                const int64_t q = PERM ? (int64_t)a.pos[s] : s;
+                const float r = a.e[q];
+                const float al = HAS_A ? a.alpha[q] : 1.f;
+                she[bi * CH + tid] = HAS_A ? al * r : r;
+                if (HAS_A) sha[bi * CH + tid] = al;
+            }
+        };
+        if (nch > 0) {
+            meta(0, 0);
+            cta_gather<B>(a, tk.begin, min(CH, tk.len), buf0);
+            cp_async_commit();
+        }
+        for (int ch = 0; ch < nch; ++ch) {
+            const int bi = ch & 1;
+            cp_async_wait_all();
+            __syncthreads();
+            if (ch + 1 < nch) {
+                meta(ch + 1, bi ^ 1);
+                cta_gather<B>(a, tk.begin + (int64_t)(ch + 1) * CH, min(CH, tk.len - (ch + 1) * CH),
+                              buf0 + (bi ^ 1) * C::BUF);
+                cp_async_commit();
+            }
+            const int cnt = min(CH, tk.len - ch * CH);
+            const float *bp = buf0 + bi * C::BUF;
+            for (int k = kstart; k < cnt; k += C::NG) {
+                const float *xk = bp + k * SB;
+                float xa[8], xb[8];
+                load_seg<8>(xk + 8 * ti, xa);
+                load_seg<8>(xk + 8 * tj, xb);
+                const float ek = she[bi * CH + k];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) gacc[i] += ek * xa[i];
+                if (HAS_A) {
+                    const float ak = sha[bi * CH + k];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) xa[i] *= ak;
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] += xa[i] * xb[j];
+            }
+        }
+        __syncthreads();
+        // fixed-order sum of the group partials into M; gradient into row B
+#pragma unroll 1
+        for (int ph = 0; ph < C::NG; ++ph) {
+            if (grp == ph) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) store_tile<8>(M + (8 * ti + i) * SB + 8 * tj, acc[i], ph > 0);
+                if (tj == 0) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        M[B * SB + 8 * ti + i] = (ph > 0 ? M[B * SB + 8 * ti + i] : 0.f) + gacc[i];
+                }
+            }
+            __syncthreads();
+        }
+        if (tk.slot >= 0) {  // a chunk of a long row: store the partial statistics
+            float *P = a.part + (int64_t)tk.slot * (B * B + B);
+            for (int e = tid; e < B * B; e += blockDim.x) {
+                const int i = e / B, j = e % B;
+                P[e] = j <= i ? M[i * SB + j] : 0.f;
+            }
+            for (int j = tid; j < B; j += blockDim.x) P[B * B + j] = M[B * SB + j];
+            continue;
+        }
+        const float lam = a.lambda * (1.0f + a.nu * (float)tk.len);
+        if (tid == 0) flag[1] = a.force_fp64 ? 1 : 0;
+        cta_dense_terms<B, SB, float>(a, M, diag0, tk.row, lam);
+        __syncthreads();
+        cta_cholesky<B, SB, float>(M, invd, diag0, &flag[1], 1e-5f);
+        if (flag[1]) {  // CTA-uniform: queue the row for the FP64 re-solve
+            if (tid == 0) {
+                const int i = atomicAdd(a.retry, 1);
+                a.retry[1 + i] = tk.row;
+            }
+            continue;
+        }
+        for (int j = tid; j < B; j += blockDim.x) xv[j] = M[B * SB + j];
+        __syncthreads();
+        cta_backsolve<B, SB, float>(M, invd, xv);
+        bool finite = true;
+        for (int j = 0; j < B; ++j) finite = finite && isfinite(xv[j]);
+        if (!finite) {
+            if (tid == 0) {
+                const int i = atomicAdd(a.retry, 1);
+                a.retry[1 + i] = tk.row;
+            }
+            continue;
+        }
+        for (int j = tid; j < B; j += blockDim.x) a.X[(int64_t)tk.row * a.d + a.p0 + j] -= xv[j];
+        cta_residual_update<B, PERM>(a, tk.begin, tk.len, xv, buf0);
+    }
+}
+
+// One block per split row: partial slots summed in slot order, then the CTA solve.
+template <int B>
+__global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_split_solve_cta(const StepArgs a) {
+    using C = CtaCfg<B>;
+    constexpr int SB = C::SB;
+    extern __shared__ float4 smem4[];
+    float *smem = reinterpret_cast<float *>(smem4);
+    float *M = smem + 2 * C::BUF + 4 * C::CH;
+    float *diag0 = M + (B + 1) * SB;
+    float *invd = diag0 + B;
+    float *xv = invd + B;
+    int *flag = reinterpret_cast<int *>(xv + B);
+    const int tid = threadIdx.x;
+    for (int i = blockIdx.x; i < a.n_split; i += gridDim.x) {
+        const SplitRow sr = a.split[i];
+        const float *P0 = a.part + (int64_t)sr.slot0 * (B * B + B);
+        for (int e = tid; e < B * B + B; e += blockDim.x) {
+            float t = 0.f;
+            for (int sl = 0; sl < sr.nslots; ++sl) t += P0[(int64_t)sl * (B * B + B) + e];
+            if (e < B * B) M[(e / B) * SB + (e % B)] = t;
+            else M[B * SB + (e - B * B)] = t;
+        }
+        if (tid == 0) flag[1] = a.force_fp64 ? 1 : 0;
+        __syncthreads();
+        const float lam = a.lambda * (1.0f + a.nu * (float)sr.len);
+        cta_dense_terms<B, SB, float>(a, M, diag0, sr.row, lam);
+        __syncthreads();
+        cta_cholesky<B, SB, float>(M, invd, diag0, &flag[1], 1e-5f);
+        bool ok = !flag[1];
+        if (ok) {
+            for (int j = tid; j < B; j += blockDim.x) xv[j] = M[B * SB + j];
+            __syncthreads();
+            cta_backsolve<B, SB, float>(M, invd, xv);
+            for (int j = 0; j < B; ++j) ok = ok && isfinite(xv[j]);
+        }
+        if (!ok) {
+            if (tid == 0) {
+                const int q = atomicAdd(a.retry, 1);
+                a.retry[1 + q] = sr.row;
+            }
+            for (int j = tid; j < B; j += blockDim.x) a.delta[(int64_t)i * B + j] = 0.f;
+        } else {
+            for (int j = tid; j < B; j += blockDim.x) {
+                a.X[(int64_t)sr.row * a.d + a.p0 + j] -= xv[j];
+                a.delta[(int64_t)i * B + j] = xv[j];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// FP64 re-solve of queued rows: statistics accumulated from scratch in FP64 by
+// the tile owners (one group, reading slices straight from global memory), the
+// blocked Cholesky in FP64, apply and residual update.
+template <int B, bool PERM, bool HAS_A>
+__global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_retry_cta(const StepArgs a) {
+    using C = CtaCfg<B>;
+    constexpr int SM = B + 1;
+    extern __shared__ float4 smem4[];
+    float *buf = reinterpret_cast<float *>(smem4);  // CH x SB staging for the residual update
+    double *M = reinterpret_cast<double *>(buf + C::BUF);  // (B+1) x (B+1)
+    double *diag0 = M + (B + 1) * SM;
+    double *invd = diag0 + B;
+    double *xd = invd + B;
+    int *flag = reinterpret_cast<int *>(xd + B);
+    float *xf = reinterpret_cast<float *>(flag + 4);
+    const int tid = threadIdx.x;
+    int ti = 0, tj = 0;
+    tri_index(tid % C::NTL, ti, tj);
+    const int count = *(volatile int *)a.retry;
+    for (int q = blockIdx.x; q < count; q += gridDim.x) {
+        const int row = a.retry[1 + q];
+        const int64_t beg = a.ptr[row], end = a.ptr[row + 1];
+        if (tid < C::NTL) {
+            double acc[8][8], g[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                g[i] = 0.0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = 0.0;
+            }
+            for (int64_t s = beg; s < end; ++s) {
+                const int64_t r = PERM ? (int64_t)a.pos[s] : s;
+                const float *f = a.F + (int64_t)a.idx[s] * a.d + a.p0;
+                const double al = HAS_A ? (double)a.alpha[r] : 1.0;
+                const double er = al * (double)a.e[r];
+                double xa[8], xb[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) { xa[i] = f[8 * ti + i]; xb[i] = f[8 * tj + i]; }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    g[i] += er * xa[i];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] += al * xa[i] * xb[j];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) M[(8 * ti + i) * SM + 8 * tj + j] = acc[i][j];
+                if (tj == 0) M[B * SM + 8 * ti + i] = g[i];
+            }
+        }
+        if (tid == 0) flag[1] = 0;
+        __syncthreads();
+        const double lam = (double)a.lambda * (1.0 + (double)a.nu * (double)(end - beg));
+        cta_dense_terms<B, SM, double>(a, M, diag0, row, lam);
+        __syncthreads();
+        cta_cholesky<B, SM, double>(M, invd, diag0, &flag[1], 1e-13);
+        bool ok = !flag[1];
+        if (ok) {
+            for (int j = tid; j < B; j += blockDim.x) xd[j] = M[B * SM + j];
+            __syncthreads();
+            cta_backsolve<B, SM, double>(M, invd, xd);
+            for (int j = 0; j < B; ++j) ok = ok && isfinite(xd[j]);
+        }
+        if (!ok) {
+            if (tid == 0) atomicAdd((unsigned long long *)&a.stats[1], 1ull);
+            __syncthreads();
+            continue;
+        }
+        for (int j = tid; j < B; j += blockDim.x) {
+            xf[j] = (float)xd[j];
+            a.X[(int64_t)row * a.d + a.p0 + j] -= xf[j];
+        }
+        __syncthreads();
+        cta_residual_update<B, PERM>(a, beg, (int)(end - beg), xf, buf);
+        if (tid == 0) atomicAdd((unsigned long long *)&a.stats[0], 1ull);
+    }
+}
+
+template <int B>
+constexpr int retry_cta_smem() {
+    return CtaCfg<B>::BUF * 4 + ((B + 1) * (B + 1) + 3 * B) * 8 + 16 + B * 4;
+}
+
+template <int B, bool PERM, bool HAS_A>
+cudaError_t launch_sparse_cta_all(const StepArgs &a, cudaStream_t s) {
+    using C = CtaCfg<B>;
+    static bool attr_done = false;
+    static int per_sm = 0;
+    constexpr int RS = 8 * (2 * TileCfg<B>::BUF + TileCfg<B>::VEC) * 4 * 32 / B;  // warps scale 1/B
+    if (!attr_done) {
+        cudaError_t e;
+        if ((e = cudaFuncSetAttribute(k_sparse_cta<B, PERM, HAS_A>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_split_solve_cta<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      C::SMEM_BYTES)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_retry_cta<B, PERM, HAS_A>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, retry_cta_smem<B>())) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_split_resid_tiled<B, PERM>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, RS)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sparse_cta<B, PERM, HAS_A>,
+                                                               C::THREADS, C::SMEM_BYTES)) != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        attr_done = true;
+    }
+    if (a.n_tasks > 0) {
+        int grid = 152 * per_sm;
+        if (grid > a.n_tasks) grid = a.n_tasks;
+        prof_mark(a.prof, K_SPARSE, s);
+        k_sparse_cta<B, PERM, HAS_A><<<grid, C::THREADS, C::SMEM_BYTES, s>>>(a);
+        prof_mark(a.prof, -1, s);
+    }
+    if (a.n_split > 0) {
+        const int g2 = a.n_split < 152 * 4 ? a.n_split : 152 * 4;
+        prof_mark(a.prof, K_SPLIT_SOLVE, s);
+        k_split_solve_cta<B><<<g2, C::THREADS, C::SMEM_BYTES, s>>>(a);
+        prof_mark(a.prof, -1, s);
+    }
+    if (a.n_stasks > 0) {
+        constexpr int WARPS = 8 * 32 / B;
+        int g3 = (a.n_stasks + WARPS - 1) / WARPS;
+        if (g3 > 152 * 8) g3 = 152 * 8;
+        prof_mark(a.prof, K_SPLIT_RESID, s);
+        k_split_resid_tiled<B, PERM><<<g3, WARPS * 32, RS, s>>>(a);
+        prof_mark(a.prof, -1, s);
+    }
+    prof_mark(a.prof, K_RETRY, s);
+    k_retry_cta<B, PERM, HAS_A><<<76, C::THREADS, retry_cta_smem<B>(), s>>>(a);
+    prof_mark(a.prof, -1, s);
+    return cudaGetLastError();
+}
+
+template <int B>
+cudaError_t launch_sparse_cta_dispatch(const StepArgs &a, cudaStream_t s) {
+    const bool perm = a.pos != nullptr, wa = a.alpha != nullptr;
+    if (perm) return wa ? launch_sparse_cta_all<B, true, true>(a, s) : launch_sparse_cta_all<B, true, false>(a, s);
+    return wa ? launch_sparse_cta_all<B, false, true>(a, s) : launch_sparse_cta_all<B, false, false>(a, s);
+}
+
+}  // namespace ials

@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(256) k_split_resid_tiled(const StepArgs a) {
     for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.n_stasks; t += nw) {
         const Task tk = a.stasks[t];
         __syncwarp();
-        if (lane < B) vv[lane] = a.delta[(int64_t)tk.srow * B + lane];
+        for (int j = lane; j < B; j += 32) vv[j] = a.delta[(int64_t)tk.srow * B + j];
         const int nch = (tk.len + CH - 1) / CH;
         int cB = 0;
         int64_t qB = 0;

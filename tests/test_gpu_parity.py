@@ -350,3 +350,65 @@ def test_unusual_dimensions(d, b):
         oracle.halfstep(P, side, d // b - 1, W, H, yhat)
     Wg, Hg = m.factors()
     assert rel_embed_err(Wg, W) <= STEP_TOL and rel_embed_err(Hg, H) <= STEP_TOL
+
+
+# --------------------------------------------------------- block sizes 64 and 128 (one CTA per row)
+
+@pytest.mark.parametrize("b", [64, 128])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_large_blocks_match_oracle(b, weighted):
+    d = 128
+    prob = small(d=d, seed=30 + b)
+    data = prob.data
+    y, a = weights(data.nnz, b) if weighted else (None, None)
+    nu = 0.5 if weighted else 0.0
+    m = Model(data, d, b, 0.1, 2e-3, nu, W0=prob.W0, H0=prob.H0, y=y, alpha=a)
+    P = oracle.Problem.from_data(data, d, b, 0.1, 2e-3, nu, y=y, alpha=a)
+    W, H = P.factors(prob.W0, prob.H0)
+    yhat = oracle.predict(P, W, H)
+    yref = 1.0 if y is None else y.astype(np.float64)
+    for k in range(d // b):
+        for side in (0, 1):
+            assert m.block_step(side, k) == 0
+            assert oracle.halfstep(P, side, k, W, H, yhat) == 0
+            Wg, Hg = m.factors()
+            assert rel_embed_err(Wg, W) <= STEP_TOL, (k, side)
+            assert rel_embed_err(Hg, H) <= STEP_TOL, (k, side)
+    e = m.residuals().astype(np.float64)
+    assert np.abs(e - (yhat - yref)).max() <= STEP_TOL * np.abs(yhat - yref).max()
+
+
+@pytest.mark.parametrize("b", [64, 128])
+def test_large_blocks_long_rows_and_epochs(b):
+    n_users, n_items, d = 700, 600, 128
+    rng = np.random.default_rng(40 + b)
+    mask = rng.random((n_users, n_items)) < 0.03
+    mask[5, :] = True
+    mask[:, 7] = True
+    u, i = np.nonzero(mask)
+    data = synth.from_pairs(n_users, n_items, u, i)
+    W0, H0 = synth.init_factors(n_users, n_items, d, 0.1 / np.sqrt(d), 4)
+    m = Model(data, d, b, 0.1, 1e-3, 0.2, W0=W0, H0=H0)
+    objs = [m.epoch(1, objective=True)[0] for _ in range(2)]
+    P = oracle.Problem.from_data(data, d, b, 0.1, 1e-3, 0.2)
+    Wr, Hr, _, trace, st = oracle.ialspp(P, 2, W0, H0, trace=True)
+    assert st == 0
+    ref = trace.reshape(2, -1)[:, -1]
+    assert np.max(np.abs(np.array(objs) - ref) / ref) <= OBJ_TOL
+    W, H = m.factors()
+    assert rel_embed_err(W, Wr) <= EMB_TOL and rel_embed_err(H, Hr) <= EMB_TOL
+
+
+def test_large_block_fp64_retry_path():
+    prob = small(d=128, seed=50)
+    data = prob.data
+    a = Model(data, 128, 64, 0.1, 1e-3, W0=prob.W0, H0=prob.H0)
+    b = Model(data, 128, 64, 0.1, 1e-3, W0=prob.W0, H0=prob.H0, force_fp64=True)
+    a.epoch(1)
+    _, st = b.epoch(1)
+    assert st == 0
+    retries, not_pd = b.stats()
+    assert retries == (data.n_users + data.n_items) * 2 and not_pd == 0
+    Wa, Ha = a.factors()
+    Wb, Hb = b.factors()
+    assert rel_embed_err(Wb, Wa) <= STEP_TOL and rel_embed_err(Hb, Ha) <= STEP_TOL
