@@ -33,9 +33,15 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = "ml20m_136k"
-WORKLOAD_DESC = ("ML20M-shaped synthetic: 136,000 users x 20,000 items, 10,000,000 positives, "
-                 "Zipf(1.05) items, lognormal(3.7,1.1) lengths in [5,8000], d=128, b=32, "
-                 "alpha0=0.1, lambda=1e-3, nu=1, seed 0")
+WORKLOADS = {
+    "ml20m_136k": ("ML20M-shaped synthetic: 136,000 users x 20,000 items, 10,000,000 positives, "
+                   "Zipf(1.05) items, lognormal(3.7,1.1) lengths in [5,8000], d=128, b=32, "
+                   "alpha0=0.1, lambda=1e-3, nu=1, seed 0"),
+    "msd_570k": ("MSD-shaped synthetic: 570,000 users x 41,000 items, 34,000,000 positives, "
+                 "Zipf(0.9) items, lognormal(3.5,1.2) lengths in [1,41000], d=1024, b=128, "
+                 "alpha0=0.02, lambda=2e-3, nu=1, seed 0"),
+}
+WORKLOAD_DESC = WORKLOADS[WORKLOAD]
 METRIC = "iALS++ epoch throughput (row-block solves/s = (|U|+|I|)*d/b per epoch)"
 
 # DRAM bytes (read + write) per launch of the dominant kernel from the ncu capture summarised
@@ -143,8 +149,8 @@ def oracle_sample(prob, frac=0.1):
     return step, n_sub + data.n_items, desc, P.n_threads
 
 
-def cpu_baseline(prob, budget_s=15.0):
-    step, rows, desc, threads = oracle_sample(prob)
+def cpu_baseline(prob, budget_s=15.0, frac=0.1):
+    step, rows, desc, threads = oracle_sample(prob, frac)
     t0 = time.perf_counter()
     n = 0
     while True:
@@ -163,8 +169,8 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2110_14044_gb300 import synth
-    prob = synth.preset(WORKLOAD, seed=0)
-    step, rows, desc, threads = oracle_sample(prob)
+    prob = synth.preset(args.workload, seed=0, **overrides(args))
+    step, rows, desc, threads = oracle_sample(prob, 0.1 if prob.d <= 256 else 0.01)
     for _ in range(args.warmup):
         step()
     t0 = time.perf_counter()
@@ -177,7 +183,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3 / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "sample": desc},
+        "config": {"workload": describe(args, prob), "sample": desc},
         "cpu_baseline": {"value": value, "unit": "rows/s", "cores": threads, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -197,7 +203,7 @@ def run_ours(args):
     build.build()
     import paper_2110_14044_gb300 as ials
 
-    prob = synth.preset(WORKLOAD, seed=0)
+    prob = synth.preset(args.workload, seed=0, **overrides(args))
     data = prob.data
     prec = _abi.PREC_BF16 if args.precision == "bf16" else _abi.PREC_FP32
     stream = torch.cuda.Stream()
@@ -288,9 +294,9 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == _abi.PREC_FP32 else "bf16",
         "data": "synthetic (seeded; no dataset in the container)",
-        "config": {"workload": WORKLOAD_DESC, "precision": args.precision,
+        "config": {"workload": describe(args, prob), "precision": args.precision,
                    "graph": not args.no_graph,
-                   "l2": "inputs larger than L2 (W 70 MB + H 10 MB + residuals 40 MB + CSR 80 MB)",
+                   "l2": "inputs larger than L2 (factors + residuals + CSR > 126 MB; no flush needed)",
                    "parallelism": f"replicas x{world}"},
         "epoch_s": ms_per_step / 1e3,
         "rows_per_s_plain": (data.n_users + data.n_items) / (ms_per_step / 1e3),
@@ -304,7 +310,7 @@ def run_ours(args):
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(prob)
+        line["cpu_baseline"] = cpu_baseline(prob, frac=0.1 if prob.d <= 256 else 0.01)
     if rank == 0:
         print(json.dumps(line), flush=True)
     m.close()
@@ -318,7 +324,7 @@ def run_ncu_step(args):
     from paper_2110_14044_gb300 import _abi, build, synth
     build.build()
     import paper_2110_14044_gb300 as ials
-    prob = synth.preset(WORKLOAD, seed=0)
+    prob = synth.preset(args.workload, seed=0, **overrides(args))
     prec = _abi.PREC_BF16 if args.precision == "bf16" else _abi.PREC_FP32
     m = ials.Model(prob.data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu, precision=prec,
                    W0=prob.W0, H0=prob.H0)
@@ -329,8 +335,27 @@ def run_ncu_step(args):
     print("ncu-step done")
 
 
+def overrides(args):
+    o = {}
+    if args.d:
+        o["d"] = args.d
+    if args.b:
+        o["b"] = args.b
+    return o
+
+
+def describe(args, prob):
+    desc = WORKLOADS[args.workload]
+    if args.d or args.b:
+        desc += f" (overridden: d={prob.d}, b={prob.b})"
+    return desc
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--d", type=int, default=0, help="override the embedding dimension")
+    ap.add_argument("--b", type=int, default=0, help="override the block size")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
