@@ -58,7 +58,10 @@ typedef enum {
 /* Arithmetic of the block step. */
 enum {
     IALS_PREC_FP32 = 0,  /* FP32 everywhere (FP64 objective, FP64 retry of failed pivots) */
-    IALS_PREC_BF16 = 1   /* BF16 tensor-core Gramian/Hessian products, FP32 accumulate */
+    IALS_PREC_BF16 = 1   /* BF16 tensor-core statistics: x = hi + lo split into two bf16,
+                          * products hi*hi + hi*lo + lo*hi accumulated in FP32 (about 16
+                          * bits); FP32 Cholesky with FP64 retry, FP64 objective.  Needs
+                          * b = 16 or 32, d % 8 == 0 and unweighted data (alpha NULL). */
 };
 
 /* ials_params.flags */

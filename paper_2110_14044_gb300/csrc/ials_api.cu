@@ -129,6 +129,7 @@ struct ials_ctx {
     cudaStream_t stream = nullptr;
     std::vector<DevBuf> bufs;
     float *W = nullptr, *H = nullptr, *e = nullptr, *y = nullptr, *alpha = nullptr;
+    __nv_bfloat16 *Wh = nullptr, *Wl = nullptr, *Hh = nullptr, *Hl = nullptr;  // BF16 mode shadows
     SideDev side[2];
     float *G = nullptr, *gram_ws = nullptr, *R = nullptr, *part = nullptr, *delta = nullptr;
     int32_t *ctl = nullptr;    // [0] work counter, [1] retry count, [2..] retry rows
@@ -264,7 +265,16 @@ ials_status step_enqueue(ials_ctx *c, int side, int block, Profiler *prof = null
     a.stats = c->stats;
     a.force_fp64 = (c->p.flags & IALS_FLAG_FORCE_FP64) ? 1 : 0;
     a.prof = prof;
-    IALS_CUDA(launch_sparse(a, s), "sparse block step");
+    a.Xh = side == 0 ? c->Wh : c->Hh;
+    a.Xl = side == 0 ? c->Wl : c->Hl;
+    a.Fh = side == 0 ? c->Hh : c->Wh;
+    a.Fl = side == 0 ? c->Hl : c->Wl;
+    if (c->p.precision == IALS_PREC_BF16) {
+        IALS_CUDA(b == 16 ? launch_sparse_bf16_b16(a, s) : launch_sparse_bf16_b32(a, s),
+                  "sparse block step (BF16)");
+    } else {
+        IALS_CUDA(launch_sparse(a, s), "sparse block step");
+    }
     return IALS_OK;
 }
 
@@ -342,6 +352,8 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
         return fail(IALS_EINVAL, "alpha0, lambda, nu must be finite and >= 0");
     if (p.precision != IALS_PREC_FP32 && p.precision != IALS_PREC_BF16)
         return fail(IALS_EINVAL, "unknown precision");
+    if (p.precision == IALS_PREC_BF16 && ((p.b != 16 && p.b != 32) || p.d % 8 != 0 || alpha))
+        return fail(IALS_EINVAL, "BF16 precision needs b = 16 or 32, d % 8 == 0 and unweighted data");
     if (n_users <= 0 || n_items <= 0) return fail(IALS_EINVAL, "n_users and n_items must be > 0");
     if (nnz < 0 || nnz >= (int64_t)1 << 31) return fail(IALS_EINVAL, "nnz must be in [0, 2^31)");
     if (!u_indptr || (nnz > 0 && !u_items)) return fail(IALS_EINVAL, "user CSR missing");
@@ -443,6 +455,12 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     } while (0)
     ALLOC(c->W, (int64_t)n_users * d, "W");
     ALLOC(c->H, (int64_t)n_items * d, "H");
+    if (p.precision == IALS_PREC_BF16) {
+        ALLOC(c->Wh, (int64_t)n_users * d, "W hi");
+        ALLOC(c->Wl, (int64_t)n_users * d, "W lo");
+        ALLOC(c->Hh, (int64_t)n_items * d, "H hi");
+        ALLOC(c->Hl, (int64_t)n_items * d, "H lo");
+    }
     ALLOC(c->e, nnz, "residuals");
     if (y) ALLOC(c->y, nnz, "y");
     if (alpha) ALLOC(c->alpha, nnz, "alpha");
@@ -500,6 +518,8 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     cudaError_t e1 = launch_init_normal(c->W, (int64_t)n_users * d, p.init_std, p.seed, 1, c->stream);
     cudaError_t e2 = launch_init_normal(c->H, (int64_t)n_items * d, p.init_std, p.seed, 2, c->stream);
     cudaError_t e3 = cudaMemsetAsync(c->stats, 0, 2 * sizeof(int64_t), c->stream);
+    if (e3 == cudaSuccess && c->Wh) e3 = launch_split_bf16(c->W, (int64_t)n_users * d, c->Wh, c->Wl, c->stream);
+    if (e3 == cudaSuccess && c->Hh) e3 = launch_split_bf16(c->H, (int64_t)n_items * d, c->Hh, c->Hl, c->stream);
     cudaError_t e4 = cudaStreamSynchronize(c->stream);
     cudaError_t e5 = launch_residual(c->side[0].ptr, c->side[0].idx, c->W, c->H, c->y, n_users, d,
                                      c->e, c->stream);
@@ -523,8 +543,17 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
         a.counter = c->ctl;
         a.retry = c->ctl + 1;
         a.stats = c->stats;
+        a.Xh = sd == 0 ? c->Wh : c->Hh;
+        a.Xl = sd == 0 ? c->Wl : c->Hl;
+        a.Fh = sd == 0 ? c->Hh : c->Wh;
+        a.Fl = sd == 0 ? c->Hl : c->Wl;
         e7 = cudaMemsetAsync(c->ctl, 0, 2 * sizeof(int32_t), c->stream);
-        if (e7 == cudaSuccess) e7 = launch_sparse(a, c->stream);
+        if (e7 == cudaSuccess) {
+            if (p.precision == IALS_PREC_BF16)
+                e7 = b == 16 ? launch_sparse_bf16_b16(a, c->stream) : launch_sparse_bf16_b32(a, c->stream);
+            else
+                e7 = launch_sparse(a, c->stream);
+        }
     }
     cudaError_t e8 = cudaStreamSynchronize(c->stream);
     for (cudaError_t e : {e1, e2, e3, e4, e5, e6, e7, e8})
@@ -593,6 +622,10 @@ ials_status ials_set_factors(ials_ctx *c, const float *W, const float *H) {
     const size_t wb = sizeof(float) * (size_t)c->n_users * c->p.d, hb = sizeof(float) * (size_t)c->n_items * c->p.d;
     if (W) IALS_CUDA(cudaMemcpyAsync(c->W, W, wb, cudaMemcpyDefault, c->stream), "copy W in");
     if (H) IALS_CUDA(cudaMemcpyAsync(c->H, H, hb, cudaMemcpyDefault, c->stream), "copy H in");
+    if (W && c->Wh)
+        IALS_CUDA(launch_split_bf16(c->W, (int64_t)c->n_users * c->p.d, c->Wh, c->Wl, c->stream), "W shadow");
+    if (H && c->Hh)
+        IALS_CUDA(launch_split_bf16(c->H, (int64_t)c->n_items * c->p.d, c->Hh, c->Hl, c->stream), "H shadow");
     // the residual cache is a function of W and H: keep it consistent
     IALS_CUDA(launch_residual(c->side[0].ptr, c->side[0].idx, c->W, c->H, c->y, c->n_users,
                               c->p.d, c->e, c->stream),

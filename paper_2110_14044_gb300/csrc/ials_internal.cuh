@@ -2,6 +2,7 @@
 // Nothing here is part of the public ABI (see include/ials.h).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -37,6 +38,20 @@ inline void prof_mark(Profiler *p, int k, cudaStream_t s) {
     if (p) p->mark(k, s);
 }
 
+#ifdef __CUDACC__
+// x -= delta for one coordinate, keeping the BF16 hi/lo shadow current (BF16 mode).
+__device__ __forceinline__ void apply_delta(float *X, __nv_bfloat16 *Xh, __nv_bfloat16 *Xl,
+                                            int64_t i, float delta) {
+    const float x = X[i] - delta;
+    X[i] = x;
+    if (Xh) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        Xh[i] = h;
+        Xl[i] = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+}
+#endif
+
 constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -68,6 +83,10 @@ struct StepArgs {
     const float *alpha;     // per interaction weights (user-major) or nullptr
     float *X;               // updated side, n_rows x d
     const float *F;         // fixed side, n_fixed x d
+    // BF16 mode: hi/lo shadows (x = hi + lo to ~16 bits) of the updated and fixed sides;
+    // nullptr in FP32 mode
+    __nv_bfloat16 *Xh, *Xl;
+    const __nv_bfloat16 *Fh, *Fl;
     const float *G;         // partial Gramian of F, d x b (row-major)
     const float *R;         // row terms alpha0 x_r G + lambda_r x_{r,pi}, n_rows x b
     int32_t n_rows, d, b, p0;
@@ -126,6 +145,9 @@ cudaError_t launch_gram64(const float *X, int64_t n, int32_t d, double *G64, dou
 cudaError_t launch_rowterm(const float *X, const int64_t *ptr, int32_t n_rows, int32_t d,
                            int32_t p0, int32_t bs, const float *G, float alpha0, float lambda,
                            float nu, float *R, cudaStream_t s);
+// BF16 hi/lo split of count floats: hi = bf16(x), lo = bf16(x - hi)
+cudaError_t launch_split_bf16(const float *X, int64_t count, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                              cudaStream_t s);
 // N(0, std^2) draws from a counter-based hash (SplitMix64 + Box-Muller)
 cudaError_t launch_init_normal(float *X, int64_t count, double std, uint64_t seed,
                                uint64_t stream_id, cudaStream_t s);
@@ -141,5 +163,8 @@ cudaError_t launch_sparse_b32(const StepArgs &a, cudaStream_t s);
 // block sizes 64 and 128 (k_sparse_b64.cu, k_sparse_b128.cu): one CTA per task
 cudaError_t launch_sparse_b64(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_sparse_b128(const StepArgs &a, cudaStream_t s);
+// BF16 mode (k_sparse_bf16.cu): tensor-core statistics for block sizes 16 and 32
+cudaError_t launch_sparse_bf16_b16(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_sparse_bf16_b32(const StepArgs &a, cudaStream_t s);
 
 }  // namespace ials

@@ -356,6 +356,16 @@ __global__ void k_init_normal(float *X, int64_t count, double std, uint64_t key)
     X[i] = (float)(std * sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));
 }
 
+__global__ void k_split_bf16(const float *__restrict__ X, int64_t count, __nv_bfloat16 *__restrict__ hi,
+                             __nv_bfloat16 *__restrict__ lo) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float x = X[i];
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
 int residual_grid(int32_t n_rows) {
     int g = (n_rows + 7) / 8;
     return g < 4 * kSMs ? (g > 0 ? g : 1) : 4 * kSMs;
@@ -499,6 +509,13 @@ cudaError_t launch_rowterm(const float *X, const int64_t *ptr, int32_t n_rows, i
     if (TN == 16) k_rowterm<256, 16><<<grid, 256, 0, s>>>(X, ptr, n_rows, d, p0, bs, G, alpha0, lambda, nu, R);
     else if (TN == 32) k_rowterm<128, 32><<<grid, 256, 0, s>>>(X, ptr, n_rows, d, p0, bs, G, alpha0, lambda, nu, R);
     else k_rowterm<64, 64><<<grid, 256, 0, s>>>(X, ptr, n_rows, d, p0, bs, G, alpha0, lambda, nu, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16(const float *X, int64_t count, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                              cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    k_split_bf16<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(X, count, hi, lo);
     return cudaGetLastError();
 }
 

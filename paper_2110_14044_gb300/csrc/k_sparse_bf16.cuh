@@ -1,0 +1,353 @@
+// Sparse block step of Algorithm 3 on BF16 tensor cores (precision IALS_PREC_BF16),
+// block sizes B = 16 and 32, one warp per task.
+//
+// The statistics of a row (Eqs. 11-12) are one small GEMM: with X the staged
+// slices (one row per interaction, B coordinates) and e the residuals,
+//     [A_r | g_r] = X^T [X | e]
+// so the residual rides as one extra column of the staged tile and the
+// gradient falls out of the same mma.sync.m16n8k16 (BF16 in, FP32 accumulate).
+// Every operand is split x = hi + lo (hi = bf16(x), lo = bf16(x - hi)) and each
+// product is compensated, hi*hi + hi*lo + lo*hi, which keeps about 16 bits
+// (the dropped lo*lo term is below 2^-16 relative).  Only the 16 x 8 output
+// tiles on or below the diagonal are formed.  The slices come from hi/lo
+// shadow copies of the factors kept in HBM (updated wherever a delta is
+// applied) and are gathered with cp.async into two staging buffers.  One
+// ldmatrix.x4.trans of a 16 x 16 block serves both as the A fragment of an
+// m-tile and as the B fragments of the two matching n-tiles.  The Newton solve
+// (warp Cholesky, FP32), apply and the FP32 residual update (x = hi + lo) are
+// those of the FP32 kernels.
+#pragma once
+
+#include "k_sparse_impl.cuh"
+
+namespace ials {
+
+template <int B>
+struct BfCfg {
+    static constexpr int MT = B / 16;           // 16-row tiles of A_r
+    static constexpr int NLOW = MT * (MT + 1);  // (m-tile, 8-column tile) pairs on/below the diagonal
+    static constexpr int SBH = B + 8;           // bf16 row stride; column B holds the residual
+    static constexpr int CH = 32;
+    static constexpr int TILE = CH * SBH;       // bf16 elements of one hi (or lo) tile
+    static constexpr int BUF_BYTES = 2 * TILE * 2;
+    static constexpr int SA = B + 4;            // float row stride of the shared A_r (in buffer 1)
+    static constexpr int WARP_BYTES = 2 * BUF_BYTES + B * 4 + 16;
+    static constexpr int WARPS = 8;
+    static constexpr int SMEM_BYTES = B * B * 4 + WARPS * WARP_BYTES;
+    static_assert(B * SA * 4 <= BUF_BYTES, "A_r must fit a staging buffer");
+    static_assert(WARP_BYTES % 16 == 0, "alignment");
+};
+
+__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const void *p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0,
+                                         unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// <v, hi + lo> over B coordinates of one staged row (16-byte shared loads).
+template <int B>
+__device__ __forceinline__ float dot_hilo(const float *v, const __nv_bfloat16 *h,
+                                          const __nv_bfloat16 *l) {
+    float t = 0.f;
+#pragma unroll
+    for (int j = 0; j < B; j += 8) {
+        const uint4 hv = *reinterpret_cast<const uint4 *>(h + j);
+        const uint4 lv = *reinterpret_cast<const uint4 *>(l + j);
+        const unsigned hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 fh = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hw[q]));
+            const float2 fl = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&lw[q]));
+            t += v[j + 2 * q] * (fh.x + fl.x) + v[j + 2 * q + 1] * (fh.y + fl.y);
+        }
+    }
+    return t;
+}
+
+// Gather the hi and lo slices of `cnt` interactions (column id of interaction k in lane k).
+template <int B>
+__device__ __forceinline__ void gather_hilo(__nv_bfloat16 *th, __nv_bfloat16 *tl,
+                                            const StepArgs &a, int c_lane, int cnt, int lane) {
+    constexpr int SBH = BfCfg<B>::SBH;
+    constexpr int HC = B / 8;          // 16-byte chunks per hi slice
+    constexpr int NCI = 2 * HC;        // per interaction (hi + lo)
+    constexpr int PASSES = 32 * NCI / 32;
+#pragma unroll
+    for (int p = 0; p < PASSES; ++p) {
+        const int f = p * 32 + lane;
+        const int k = f / NCI, v = f % NCI;
+        const int ck = __shfl_sync(kFull, c_lane, k);
+        if (k < cnt) {
+            const int half = v / HC, vc = v % HC;
+            const __nv_bfloat16 *src = (half ? a.Fl : a.Fh) + (int64_t)ck * a.d + a.p0 + vc * 8;
+            __nv_bfloat16 *dst = (half ? tl : th) + k * SBH + vc * 8;
+            cp_async16(dst, src);
+        }
+    }
+}
+
+template <int B, bool PERM>
+__global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
+    using C = BfCfg<B>;
+    constexpr int SBH = C::SBH, CH = C::CH, MT = C::MT, SA = C::SA;
+    extern __shared__ float4 smem4[];
+    char *sm = reinterpret_cast<char *>(smem4);
+    float *sGpp = reinterpret_cast<float *>(sm);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < B * B; i += blockDim.x)
+        sGpp[i] = a.alpha0 * a.G[(int64_t)(a.p0 + i / B) * B + (i % B)];
+    char *wb = sm + B * B * 4 + warp * C::WARP_BYTES;
+    // staging buffer bi: hi tile at wb + bi * BUF_BYTES, lo tile right after it
+    auto th_of = [&](int bi) { return reinterpret_cast<__nv_bfloat16 *>(wb + bi * C::BUF_BYTES); };
+    float *vv = reinterpret_cast<float *>(wb + 2 * C::BUF_BYTES);
+    for (int i = lane; i < 2 * C::BUF_BYTES / 16; i += 32)
+        reinterpret_cast<uint4 *>(wb)[i] = make_uint4(0u, 0u, 0u, 0u);  // padding columns stay zero
+    __syncthreads();
+    float *As = reinterpret_cast<float *>(wb + C::BUF_BYTES);  // A_r and the factor copy reuse buffer 1
+    WarpSmem w;
+    w.v = vv;
+    w.L = As;
+    const int col = lane % B, sub = lane / B;
+    for (;;) {
+        int tsk = 0;
+        if (lane == 0) tsk = atomicAdd(a.counter, 1);
+        tsk = __shfl_sync(kFull, tsk, 0);
+        if (tsk >= a.n_tasks) break;
+        const Task tk = a.tasks[tsk];
+        const int nch = (tk.len + CH - 1) / CH;
+        float acc[C::NLOW][4], gac[MT][4];
+#pragma unroll
+        for (int t = 0; t < C::NLOW; ++t)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[t][q] = 0.f;
+#pragma unroll
+        for (int t = 0; t < MT; ++t)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) gac[t][q] = 0.f;
+        int cB = 0;
+        int64_t qB = 0, q0 = 0;
+        float eB = 0.f;
+        auto load_meta = [&](int j) {
+            const int cnt = min(CH, tk.len - j * CH);
+            if (lane < cnt) {
+                const int64_t s = tk.begin + (int64_t)j * CH + lane;
+                cB = a.idx[s];
+                qB = PERM ? (int64_t)a.pos[s] : s;
+                eB = a.e[qB];
+            }
+        };
+        auto issue = [&](int j, int bi) {
+            const int cnt = min(CH, tk.len - j * CH);
+            __nv_bfloat16 *th = th_of(bi), *tl = th + C::TILE;
+            if (lane < cnt) {  // residual column
+                const __nv_bfloat16 h = __float2bfloat16_rn(eB);
+                th[lane * SBH + B] = h;
+                tl[lane * SBH + B] = __float2bfloat16_rn(eB - __bfloat162float(h));
+            } else if (lane < ((cnt + 15) & ~15)) {  // rows past the end of a short chunk: zero
+#pragma unroll
+                for (int v = 0; v < SBH / 8; ++v) {
+                    reinterpret_cast<uint4 *>(th + lane * SBH)[v] = make_uint4(0u, 0u, 0u, 0u);
+                    reinterpret_cast<uint4 *>(tl + lane * SBH)[v] = make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
+            gather_hilo<B>(th, tl, a, cB, cnt, lane);
+            cp_async_commit();
+        };
+        if (nch > 0) {
+            load_meta(0);
+            q0 = qB;
+            issue(0, 0);
+            if (nch > 1) load_meta(1);
+        }
+        for (int ch = 0; ch < nch; ++ch) {
+            const int bi = ch & 1;
+            cp_async_wait_all();
+            __syncwarp();
+            if (ch + 1 < nch) {
+                issue(ch + 1, bi ^ 1);
+                if (ch + 2 < nch) load_meta(ch + 2);
+            }
+            const int cnt = min(CH, tk.len - ch * CH);
+            const __nv_bfloat16 *th = th_of(bi), *tl = th + C::TILE;
+            const int ksteps = (cnt + 15) >> 4;
+            const int mj = lane >> 3, mr = lane & 7;
+            for (int ks = 0; ks < ksteps; ++ks) {
+                unsigned Rh[MT][4], Rl[MT][4], E[4];
+#pragma unroll
+                for (int gi = 0; gi < MT; ++gi) {
+                    const int off = (ks * 16 + (mj >> 1) * 8 + mr) * SBH + gi * 16 + (mj & 1) * 8;
+                    ldsm_x4_t(Rh[gi], th + off);
+                    ldsm_x4_t(Rl[gi], tl + off);
+                }
+                {
+                    const __nv_bfloat16 *base = mj < 2 ? th : tl;
+                    ldsm_x4_t(E, base + (ks * 16 + (mj & 1) * 8 + mr) * SBH + B);
+                }
+                int t = 0;
+#pragma unroll
+                for (int i = 0; i < MT; ++i) {
+#pragma unroll
+                    for (int n = 0; n <= 2 * i + 1; ++n) {
+                        const int g2 = n >> 1, h = n & 1;
+                        mma_bf16(acc[t], Rh[i], Rh[g2][h], Rh[g2][h + 2]);
+                        mma_bf16(acc[t], Rh[i], Rl[g2][h], Rl[g2][h + 2]);
+                        mma_bf16(acc[t], Rl[i], Rh[g2][h], Rh[g2][h + 2]);
+                        ++t;
+                    }
+                    mma_bf16(gac[i], Rh[i], E[0], E[1]);
+                    mma_bf16(gac[i], Rh[i], E[2], E[3]);
+                    mma_bf16(gac[i], Rl[i], E[0], E[1]);
+                }
+            }
+            __syncwarp();
+        }
+        // fragments -> shared A_r (buffer 1) and gradient (vv)
+        {
+            int t = 0;
+            const int r = lane >> 2, c2 = 2 * (lane & 3);
+#pragma unroll
+            for (int i = 0; i < MT; ++i) {
+#pragma unroll
+                for (int n = 0; n <= 2 * i + 1; ++n) {
+                    *reinterpret_cast<float2 *>(As + (16 * i + r) * SA + 8 * n + c2) = make_float2(acc[t][0], acc[t][1]);
+                    *reinterpret_cast<float2 *>(As + (16 * i + r + 8) * SA + 8 * n + c2) = make_float2(acc[t][2], acc[t][3]);
+                    ++t;
+                }
+                if ((lane & 3) == 0) {
+                    vv[16 * i + r] = gac[i][0];
+                    vv[16 * i + r + 8] = gac[i][2];
+                }
+            }
+        }
+        __syncwarp();
+        float A[B];
+#pragma unroll
+        for (int j = 0; j < B; j += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(As + col * SA + j);
+            A[j] = v.x; A[j + 1] = v.y; A[j + 2] = v.z; A[j + 3] = v.w;
+        }
+        float g = vv[col];
+        __syncwarp();
+        if (tk.slot >= 0) {  // a chunk of a long row: store the partial statistics (row col)
+            if (sub == 0) {
+                float *P = a.part + (int64_t)tk.slot * (B * B + B);
+#pragma unroll
+                for (int j = 0; j < B; j += 4)
+                    *reinterpret_cast<float4 *>(P + col * B + j) = make_float4(A[j], A[j + 1], A[j + 2], A[j + 3]);
+                P[B * B + col] = g;
+            }
+            continue;
+        }
+        const int row = tk.row;
+        const float lam = a.lambda * (1.0f + a.nu * (float)tk.len);
+#pragma unroll
+        for (int j = 0; j < B; ++j) A[j] += sGpp[col * B + j] + (j == col ? lam : 0.f);
+        g += a.R[(int64_t)row * B + col];
+        float delta;
+        if (!chol_solve<B>(A, g, col, sub, w, a.force_fp64 != 0, delta)) {
+            queue_retry(a, lane, row);
+            continue;
+        }
+        if (sub == 0) apply_delta(a.X, a.Xh, a.Xl, (int64_t)row * a.d + a.p0 + col, delta);
+        __syncwarp();
+        if (sub == 0) vv[col] = delta;
+        __syncwarp();
+        if (nch == 1) {  // the slices are still in buffer 0
+            const __nv_bfloat16 *th = th_of(0), *tl = th + C::TILE;
+            if (lane < tk.len) a.e[q0] -= dot_hilo<B>(vv, th + lane * SBH, tl + lane * SBH);
+            __syncwarp();
+        } else if (nch > 1) {
+            int64_t qc = 0;
+            auto meta2 = [&](int j) {
+                const int cnt = min(CH, tk.len - j * CH);
+                if (lane < cnt) {
+                    const int64_t s = tk.begin + (int64_t)j * CH + lane;
+                    cB = a.idx[s];
+                    qB = PERM ? (int64_t)a.pos[s] : s;
+                }
+            };
+            meta2(0);
+            qc = qB;
+            gather_hilo<B>(th_of(0), th_of(0) + C::TILE, a, cB, min(CH, tk.len), lane);
+            cp_async_commit();
+            meta2(1);
+            for (int ch = 0; ch < nch; ++ch) {
+                const int bi = ch & 1;
+                cp_async_wait_all();
+                __syncwarp();
+                int64_t qn = 0;
+                if (ch + 1 < nch) {
+                    gather_hilo<B>(th_of(bi ^ 1), th_of(bi ^ 1) + C::TILE, a, cB,
+                                   min(CH, tk.len - (ch + 1) * CH), lane);
+                    cp_async_commit();
+                    qn = qB;
+                    if (ch + 2 < nch) meta2(ch + 2);
+                }
+                const int cnt = min(CH, tk.len - ch * CH);
+                const __nv_bfloat16 *th = th_of(bi), *tl = th + C::TILE;
+                if (lane < cnt) a.e[qc] -= dot_hilo<B>(vv, th + lane * SBH, tl + lane * SBH);
+                __syncwarp();
+                qc = qn;
+            }
+        }
+    }
+}
+
+template <int B, bool PERM>
+cudaError_t launch_sparse_bf16_all(const StepArgs &a, cudaStream_t s) {
+    using C = BfCfg<B>;
+    using T = TileCfg<B>;
+    constexpr int RS = 8 * (2 * T::BUF + T::VEC) * 4;
+    static bool attr_done = false;
+    static int per_sm = 0;
+    if (!attr_done) {
+        cudaError_t e;
+        if ((e = cudaFuncSetAttribute(k_sparse_bf16<B, PERM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      C::SMEM_BYTES)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_split_solve<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      split_solve_smem<B>())) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_split_resid_tiled<B, PERM>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, RS)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sparse_bf16<B, PERM>,
+                                                               C::WARPS * 32, C::SMEM_BYTES)) != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        attr_done = true;
+    }
+    if (a.n_tasks > 0) {
+        int grid = 152 * per_sm;
+        const int need = (a.n_tasks + C::WARPS - 1) / C::WARPS;
+        if (grid > need) grid = need;
+        prof_mark(a.prof, K_SPARSE, s);
+        k_sparse_bf16<B, PERM><<<grid, C::WARPS * 32, C::SMEM_BYTES, s>>>(a);
+        prof_mark(a.prof, -1, s);
+    }
+    if (a.n_split > 0) {
+        const int g2 = a.n_split < 152 * 8 ? a.n_split : 152 * 8;
+        prof_mark(a.prof, K_SPLIT_SOLVE, s);
+        k_split_solve<B><<<g2, 256, split_solve_smem<B>(), s>>>(a);
+        prof_mark(a.prof, -1, s);
+    }
+    if (a.n_stasks > 0) {
+        int g3 = (a.n_stasks + 7) / 8;
+        if (g3 > 152 * 8) g3 = 152 * 8;
+        prof_mark(a.prof, K_SPLIT_RESID, s);
+        k_split_resid_tiled<B, PERM><<<g3, 256, RS, s>>>(a);
+        prof_mark(a.prof, -1, s);
+    }
+    prof_mark(a.prof, K_RETRY, s);
+    k_retry<B, PERM, false><<<38, 128, 0, s>>>(a);
+    prof_mark(a.prof, -1, s);
+    return cudaGetLastError();
+}
+
+}  // namespace ials

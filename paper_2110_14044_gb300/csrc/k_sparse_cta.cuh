@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_sparse_cta(const StepArg
             }
             continue;
         }
-        for (int j = tid; j < B; j += blockDim.x) a.X[(int64_t)tk.row * a.d + a.p0 + j] -= xv[j];
+        for (int j = tid; j < B; j += blockDim.x) apply_delta(a.X, a.Xh, a.Xl, (int64_t)tk.row * a.d + a.p0 + j, xv[j]);
         cta_residual_update<B, PERM>(a, tk.begin, tk.len, xv, buf0);
     }
 }
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_split_solve_cta(const St
             for (int j = tid; j < B; j += blockDim.x) a.delta[(int64_t)i * B + j] = 0.f;
         } else {
             for (int j = tid; j < B; j += blockDim.x) {
-                a.X[(int64_t)sr.row * a.d + a.p0 + j] -= xv[j];
+                apply_delta(a.X, a.Xh, a.Xl, (int64_t)sr.row * a.d + a.p0 + j, xv[j]);
                 a.delta[(int64_t)i * B + j] = xv[j];
             }
         }
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_retry_cta(const StepArgs
         }
         for (int j = tid; j < B; j += blockDim.x) {
             xf[j] = (float)xd[j];
-            a.X[(int64_t)row * a.d + a.p0 + j] -= xf[j];
+            apply_delta(a.X, a.Xh, a.Xl, (int64_t)row * a.d + a.p0 + j, xf[j]);
         }
         __syncthreads();
         cta_residual_update<B, PERM>(a, beg, (int)(end - beg), xf, buf);

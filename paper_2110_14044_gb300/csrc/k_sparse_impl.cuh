@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(256, 2) k_sparse(const StepArgs a) {
             queue_retry(a, lane, row);
             continue;
         }
-        if (sub == 0) a.X[(int64_t)row * a.d + a.p0 + col] -= delta;
+        if (sub == 0) apply_delta(a.X, a.Xh, a.Xl, (int64_t)row * a.d + a.p0 + col, delta);
         __syncwarp();
         if (sub == 0) w.v[col] = delta;
         __syncwarp();
@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
             queue_retry(a, lane, row);
             continue;
         }
-        if (sub == 0) a.X[(int64_t)row * a.d + a.p0 + col] -= delta;
+        if (sub == 0) apply_delta(a.X, a.Xh, a.Xl, (int64_t)row * a.d + a.p0 + col, delta);
         __syncwarp();
         if (sub == 0) vv[col] = delta;
         __syncwarp();
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(256) k_split_solve(const StepArgs a) {
                 queue_retry(a, lane, sr.row);
                 delta = 0.f;  // k_split_resid leaves the row's residuals alone
             } else if (sub == 0) {
-                a.X[(int64_t)sr.row * a.d + a.p0 + col] -= delta;
+                apply_delta(a.X, a.Xh, a.Xl, (int64_t)sr.row * a.d + a.p0 + col, delta);
             }
             if (sub == 0) a.delta[(int64_t)i * B + col] = delta;
         }
@@ -776,7 +776,7 @@ __global__ void __launch_bounds__(128) k_retry(const StepArgs a) {
             else if (col == k) x = xk;
         }
         const float delta = (float)x;
-        if (sub == 0) a.X[(int64_t)row * a.d + a.p0 + col] -= delta;
+        if (sub == 0) apply_delta(a.X, a.Xh, a.Xl, (int64_t)row * a.d + a.p0 + col, delta);
         __syncwarp();
         if (sub == 0) sv[warp][col] = (double)delta;
         __syncwarp();

@@ -1,0 +1,121 @@
+"""The BF16 tensor-core path (precision IALS_PREC_BF16) against the FP64 oracle.
+
+The BF16 form must stay within 1e-3 relative objective of the oracle per epoch.
+Each product keeps about 16 bits (hi*hi + hi*lo + lo*hi), so block steps are
+held to 1e-3 relative embedding error and whole runs are reported.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_14044_gb300 import _abi, synth
+
+pytestmark = pytest.mark.gpu
+
+BF16_OBJ_TOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_14044_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def Model(*a, **k):
+    import paper_2110_14044_gb300 as ials
+    return ials.Model(*a, precision=_abi.PREC_BF16, **k)
+
+
+def rel_embed_err(X, Xref):
+    X = np.asarray(X, np.float64)
+    Xref = np.asarray(Xref, np.float64)
+    nref = np.linalg.norm(Xref, axis=1)
+    floor = max(1e-6 * np.median(nref), 1e-30)
+    return float(np.max(np.linalg.norm(X - Xref, axis=1) / np.maximum(nref, floor)))
+
+
+@pytest.mark.parametrize("d,b", [(32, 16), (32, 32), (128, 32)])
+def test_bf16_epochs_within_objective_tolerance(d, b):
+    prob = synth.preset("parity_2k", seed=3, d=d, b=b)
+    data = prob.data
+    m = Model(data, d, b, prob.alpha0, prob.lam, 0.5, W0=prob.W0, H0=prob.H0)
+    objs = []
+    for _ in range(prob.epochs):
+        o, st = m.epoch(1, objective=True)
+        assert st == 0
+        objs.append(o)
+    P = oracle.Problem.from_data(data, d, b, prob.alpha0, prob.lam, 0.5)
+    Wr, Hr, _, trace, st = oracle.ialspp(P, prob.epochs, prob.W0, prob.H0, trace=True)
+    ref = trace.reshape(prob.epochs, -1)[:, -1]
+    rel = np.abs(np.array(objs) - ref) / ref
+    W, H = m.factors()
+    print(f"bf16 d={d} b={b}: max rel objective {rel.max():.2e}, "
+          f"embedding W {rel_embed_err(W, Wr):.2e} H {rel_embed_err(H, Hr):.2e}")
+    assert rel.max() <= BF16_OBJ_TOL
+    assert rel_embed_err(W, Wr) <= 5e-2 and rel_embed_err(H, Hr) <= 5e-2
+
+
+@pytest.mark.parametrize("b", [16, 32])
+def test_bf16_block_steps(b):
+    d = 64
+    prob = synth.preset("parity_2k", seed=b, n_users=300, n_items=200, nnz=6000, len_max=200, d=d)
+    data = prob.data
+    m = Model(data, d, b, 0.1, 2e-3, 0.3, W0=prob.W0, H0=prob.H0)
+    P = oracle.Problem.from_data(data, d, b, 0.1, 2e-3, 0.3)
+    W, H = P.factors(prob.W0, prob.H0)
+    yhat = oracle.predict(P, W, H)
+    for k in range(2):
+        for side in (0, 1):
+            assert m.block_step(side, k) == 0
+            oracle.halfstep(P, side, k, W, H, yhat)
+            Wg, Hg = m.factors()
+            assert rel_embed_err(Wg, W) <= 1e-3 and rel_embed_err(Hg, H) <= 1e-3, (k, side)
+    e = m.residuals().astype(np.float64)
+    assert np.abs(e - (yhat - 1.0)).max() <= 1e-3 * np.abs(yhat - 1.0).max()
+
+
+def test_bf16_long_rows_and_determinism():
+    n_users, n_items, d, b = 700, 600, 32, 32
+    rng = np.random.default_rng(5)
+    mask = rng.random((n_users, n_items)) < 0.03
+    mask[5, :] = True
+    mask[:, 7] = True
+    u, i = np.nonzero(mask)
+    data = synth.from_pairs(n_users, n_items, u, i)
+    W0, H0 = synth.init_factors(n_users, n_items, d, 0.1 / np.sqrt(d), 5)
+    runs = []
+    for graph in (False, True):
+        m = Model(data, d, b, 0.1, 1e-3, 0.2, W0=W0, H0=H0, graph=graph)
+        o, st = m.epoch(2, objective=True)
+        assert st == 0
+        runs.append((o, *m.factors()))
+    np.testing.assert_array_equal(runs[0][1], runs[1][1])
+    np.testing.assert_array_equal(runs[0][2], runs[1][2])
+    P = oracle.Problem.from_data(data, d, b, 0.1, 1e-3, 0.2)
+    Wr, Hr, _, _, _ = oracle.ialspp(P, 2, W0, H0)
+    ref = oracle.objective(P, Wr, Hr)
+    assert abs(runs[0][0] - ref) / ref <= BF16_OBJ_TOL
+
+
+def test_bf16_fp64_retry_updates_shadows():
+    prob = synth.preset("parity_2k", seed=7, n_users=300, n_items=200, nnz=6000, len_max=200, d=32, b=16)
+    a = Model(prob.data, 32, 16, 0.1, 1e-3, W0=prob.W0, H0=prob.H0)
+    b = Model(prob.data, 32, 16, 0.1, 1e-3, W0=prob.W0, H0=prob.H0, force_fp64=True)
+    oa, _ = a.epoch(2, objective=True)
+    ob, st = b.epoch(2, objective=True)
+    assert st == 0 and b.stats()[0] > 0
+    assert abs(oa - ob) / oa <= 1e-4
+
+
+def test_bf16_rejects_unsupported_inputs():
+    prob = synth.preset("parity_2k", seed=8, n_users=50, n_items=40, nnz=500, len_max=40, d=32, b=8)
+    with pytest.raises(_abi.IalsError):
+        Model(prob.data, 32, 8, 0.1, 1e-3)   # b = 8
+    with pytest.raises(_abi.IalsError):
+        Model(prob.data, 36, 4, 0.1, 1e-3)   # b = 4, d % 8 != 0
+    with pytest.raises(_abi.IalsError):
+        Model(prob.data, 32, 16, 0.1, 1e-3, alpha=np.ones(prob.data.nnz, np.float32))
