@@ -174,6 +174,15 @@ ials_status ials_work_model(ials_ctx *ctx, double *bytes, double *flops, int32_t
 ials_status ials_partial_gramian(const float *X, int64_t n, int32_t d, int32_t p0, int32_t bs,
                                  float *G, void *cuda_stream);
 
+/* Partial Gramian on the tcgen05 tensor cores (Eq. 10): X is split into BF16
+ * hi/lo halves and G = Xh^T Xh_pi + Xh^T Xl_pi + Xl^T Xh_pi is accumulated in
+ * FP32 (about 16 bits).  Needs d % 8 == 0, bs in {16, 32}, p0 % 8 == 0.
+ * X (n x d float32) and G (d x bs float32) are device arrays; temporaries are
+ * allocated per call.  Synchronous.  IALS_ETIMEDOUT if a bounded device wait
+ * gave up. */
+ials_status ials_partial_gramian_bf16(const float *X, int64_t n, int32_t d, int32_t p0, int32_t bs,
+                                      float *G, void *cuda_stream);
+
 /* The same partial Gramian for callers that cannot allocate device memory:
  * code whose device memory belongs to another allocator (a framework's caching
  * allocator, a fixed arena) or a latency-bound loop in which cudaMalloc /

@@ -28,7 +28,7 @@ EXPORTS = (
     "ials_create", "ials_destroy", "ials_epoch", "ials_objective", "ials_get_factors",
     "ials_set_factors", "ials_recompute_residuals", "ials_block_step", "ials_get_residuals",
     "ials_last_stats", "ials_partial_gramian", "ials_last_error", "ials_profile_epochs",
-    "ials_work_model", "ials_partial_gramian_noalloc",
+    "ials_work_model", "ials_partial_gramian_noalloc", "ials_partial_gramian_bf16",
 )
 
 KERNEL_KINDS = ("residual", "gram", "rowterm", "sparse", "split_solve", "split_resid", "retry",
@@ -76,6 +76,7 @@ def lib():
             "ials_profile_epochs": ([vp, i32, vp, vp, i32, C.POINTER(C.c_double)], st),
             "ials_work_model": ([vp, vp, vp, i32], st),
             "ials_partial_gramian_noalloc": ([vp, i64, i32, i32, i32, vp, vp], st),
+            "ials_partial_gramian_bf16": ([vp, i64, i32, i32, i32, vp, vp], st),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -207,3 +208,9 @@ def ials_partial_gramian_noalloc(X, n, d, p0, bs, G, stream=None):
     """Partial Gramian that allocates nothing (fixed 8 MiB device scratch; enqueue only)."""
     return _check(lib().ials_partial_gramian_noalloc(_ptr(X), int(n), int(d), int(p0), int(bs),
                                                      _ptr(G), _stream(stream)))
+
+
+def ials_partial_gramian_bf16(X, n, d, p0, bs, G, stream=None):
+    """Partial Gramian on tcgen05 tensor cores (BF16 hi/lo compensated, FP32 accumulate)."""
+    return _check(lib().ials_partial_gramian_bf16(_ptr(X), int(n), int(d), int(p0), int(bs), _ptr(G),
+                                                  _stream(stream)))

@@ -130,6 +130,8 @@ struct ials_ctx {
     std::vector<DevBuf> bufs;
     float *W = nullptr, *H = nullptr, *e = nullptr, *y = nullptr, *alpha = nullptr;
     __nv_bfloat16 *Wh = nullptr, *Wl = nullptr, *Hh = nullptr, *Hl = nullptr;  // BF16 mode shadows
+    GramMaps maps[2];          // BF16 mode: tensor maps of the W (0) and H (1) shadows
+    int32_t *dev_err = nullptr;  // nonzero if a bounded device wait gave up
     SideDev side[2];
     float *G = nullptr, *gram_ws = nullptr, *R = nullptr, *part = nullptr, *delta = nullptr;
     int32_t *ctl = nullptr;    // [0] work counter, [1] retry count, [2..] retry rows
@@ -228,7 +230,12 @@ ials_status step_enqueue(ials_ctx *c, int side, int block, Profiler *prof = null
     const int64_t n_fixed = side == 0 ? c->n_items : c->n_users;
     cudaStream_t s = c->stream;
     prof_mark(prof, K_GRAM, s);
-    IALS_CUDA(launch_gram(F, n_fixed, d, p0, b, c->G, c->gram_ws, s), "partial Gramian");
+    if (c->p.precision == IALS_PREC_BF16) {
+        IALS_CUDA(launch_gram_tc(c->maps[side == 0 ? 1 : 0], n_fixed, d, p0, b, c->G, c->gram_ws, c->dev_err, s),
+                  "partial Gramian (tcgen05)");
+    } else {
+        IALS_CUDA(launch_gram(F, n_fixed, d, p0, b, c->G, c->gram_ws, s), "partial Gramian");
+    }
     prof_mark(prof, K_ROWTERM, s);
     IALS_CUDA(launch_rowterm(X, sd.ptr, sd.n_rows, d, p0, b, c->G, (float)c->p.alpha0,
                              (float)c->p.lambda, (float)c->p.nu, c->R, s),
@@ -297,6 +304,10 @@ ials_status finish(ials_ctx *c) {
     IALS_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
     int64_t st[2];
     IALS_CUDA(cudaMemcpy(st, c->stats, sizeof(st), cudaMemcpyDeviceToHost), "stats");
+    int32_t derr = 0;
+    IALS_CUDA(cudaMemcpy(&derr, c->dev_err, sizeof(derr), cudaMemcpyDeviceToHost), "device error flag");
+    if (derr != 0)
+        return fail(IALS_ETIMEDOUT, "a bounded device wait gave up (code " + std::to_string(derr) + ")");
     if (st[1] > 0)
         return fail(IALS_ENOTPD, std::to_string(st[1]) +
                                      " row(s) had a Hessian that is not positive definite in FP64");
@@ -482,8 +493,10 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     const int32_t max_slots = std::max(c->side[0].n_slots, c->side[1].n_slots);
     const int32_t max_split = std::max(c->side[0].n_split, c->side[1].n_split);
     ALLOC(c->G, (int64_t)d * b, "partial Gramian");
-    ALLOC(c->gram_ws, std::max(gram_ws_floats(n_items, d, b), gram_ws_floats(n_users, d, b)),
+    ALLOC(c->gram_ws, std::max(std::max(gram_ws_floats(n_items, d, b), gram_ws_floats(n_users, d, b)),
+                               std::max(gram_tc_ws_floats(n_items, d, b), gram_tc_ws_floats(n_users, d, b))),
           "Gramian workspace");
+    ALLOC(c->dev_err, 1, "error flag");
     ALLOC(c->R, max_rows * b, "row terms");
     ALLOC(c->part, (int64_t)max_slots * (b * b + b), "split partials");
     ALLOC(c->delta, (int64_t)max_split * b, "split deltas");
@@ -520,6 +533,13 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     cudaError_t e3 = cudaMemsetAsync(c->stats, 0, 2 * sizeof(int64_t), c->stream);
     if (e3 == cudaSuccess && c->Wh) e3 = launch_split_bf16(c->W, (int64_t)n_users * d, c->Wh, c->Wl, c->stream);
     if (e3 == cudaSuccess && c->Hh) e3 = launch_split_bf16(c->H, (int64_t)n_items * d, c->Hh, c->Hl, c->stream);
+    if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->dev_err, 0, sizeof(int32_t), c->stream);
+    if (e3 == cudaSuccess && c->Wh &&
+        (!make_gram_maps(c->maps[0], c->Wh, c->Wl, n_users, d, b) ||
+         !make_gram_maps(c->maps[1], c->Hh, c->Hl, n_items, d, b))) {
+        delete c;
+        return fail(IALS_ECUDA, "could not encode TMA tensor maps (cuTensorMapEncodeTiled)");
+    }
     cudaError_t e4 = cudaStreamSynchronize(c->stream);
     cudaError_t e5 = launch_residual(c->side[0].ptr, c->side[0].idx, c->W, c->H, c->y, n_users, d,
                                      c->e, c->stream);
@@ -737,6 +757,40 @@ ials_status ials_work_model(ials_ctx *c, double *bytes, double *flops, int32_t n
         bytes[k] = k < K_COUNT ? B[k] : 0.0;
         flops[k] = k < K_COUNT ? F[k] : 0.0;
     }
+    return IALS_OK;
+}
+
+ials_status ials_partial_gramian_bf16(const float *X, int64_t n, int32_t d, int32_t p0, int32_t bs,
+                                      float *G, void *cuda_stream) {
+    if (!X || !G || n < 0 || d < 8 || d % 8 != 0 || (bs != 16 && bs != 32) || p0 < 0 || p0 % 8 != 0 ||
+        p0 + bs > d)
+        return fail(IALS_EINVAL, "bad BF16 Gramian arguments (d % 8 == 0, bs in {16, 32}, p0 % 8 == 0)");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int64_t count = n * (int64_t)d;
+    const int64_t wsn = std::max<int64_t>(gram_tc_ws_floats(n, d, bs), 1);
+    void *buf = nullptr;
+    const size_t bytes = sizeof(__nv_bfloat16) * 2 * (size_t)std::max<int64_t>(count, 1) + sizeof(float) * wsn + 256;
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(IALS_ENOMEM, "BF16 Gramian workspace");
+    }
+    __nv_bfloat16 *hi = static_cast<__nv_bfloat16 *>(buf), *lo = hi + std::max<int64_t>(count, 1);
+    float *ws = reinterpret_cast<float *>(lo + std::max<int64_t>(count, 1));
+    int32_t *err = reinterpret_cast<int32_t *>(ws + wsn);
+    GramMaps maps;
+    ials_status st = IALS_OK;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = launch_split_bf16(X, count, hi, lo, s);
+    if (e == cudaSuccess && n > 0 && !make_gram_maps(maps, hi, lo, n, d, bs)) st = fail(IALS_ECUDA, "tensor maps");
+    if (e == cudaSuccess && st == IALS_OK) e = launch_gram_tc(maps, n, d, p0, bs, G, ws, err, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    int32_t derr = 0;
+    if (e == cudaSuccess && e2 == cudaSuccess) cudaMemcpy(&derr, err, sizeof(derr), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (st != IALS_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "BF16 partial Gramian");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "synchronize");
+    if (derr) return fail(IALS_ETIMEDOUT, "a bounded device wait gave up");
     return IALS_OK;
 }
 

@@ -141,6 +141,21 @@ cudaError_t launch_gram_capped(const float *X, int64_t n, int32_t d, int32_t p0,
 int64_t gram64_ws_doubles(int64_t n, int32_t d);
 cudaError_t launch_gram64(const float *X, int64_t n, int32_t d, double *G64, double *ws,
                           cudaStream_t s);
+// Fixed-order sum of nsplit partial d x bs tiles into G.
+cudaError_t launch_gram_reduce(const float *ws, int nsplit, int64_t count, float *G, cudaStream_t s);
+
+// tcgen05 partial Gramian (k_tc_gram.cu): TMA descriptors of one BF16 hi/lo pair
+// (opaque CUtensorMap storage) and the launcher; err receives a nonzero code if
+// a bounded wait gave up.
+struct alignas(64) GramMaps {
+    unsigned char ah[128], al[128], bh[128], bl[128];
+};
+bool make_gram_maps(GramMaps &g, const __nv_bfloat16 *hi, const __nv_bfloat16 *lo, int64_t rows, int32_t d,
+                    int32_t b);
+int64_t gram_tc_ws_floats(int64_t n, int32_t d, int32_t bs);
+cudaError_t launch_gram_tc(const GramMaps &g, int64_t n, int32_t d, int32_t p0, int32_t bs, float *G, float *ws,
+                           int32_t *err, cudaStream_t s);
+
 // Row terms R[r] = alpha0 * X[r] G + lambda (1 + nu n_r) X[r, p0:p0+bs]  (n_rows x bs)
 cudaError_t launch_rowterm(const float *X, const int64_t *ptr, int32_t n_rows, int32_t d,
                            int32_t p0, int32_t bs, const float *G, float alpha0, float lambda,

@@ -484,6 +484,11 @@ cudaError_t launch_gram_capped(const float *X, int64_t n, int32_t d, int32_t p0,
     return cudaGetLastError();
 }
 
+cudaError_t launch_gram_reduce(const float *ws, int nsplit, int64_t count, float *G, cudaStream_t s) {
+    k_gram_reduce<float><<<(unsigned)((count + 255) / 256), 256, 0, s>>>(ws, nsplit, count, G);
+    return cudaGetLastError();
+}
+
 int64_t gram64_ws_doubles(int64_t n, int32_t d) {
     GramPlan p = gram_plan(n, d, d);
     return (int64_t)p.nsplit * d * d;

@@ -119,3 +119,21 @@ def test_bf16_rejects_unsupported_inputs():
         Model(prob.data, 36, 4, 0.1, 1e-3)   # b = 4, d % 8 != 0
     with pytest.raises(_abi.IalsError):
         Model(prob.data, 32, 16, 0.1, 1e-3, alpha=np.ones(prob.data.nnz, np.float32))
+
+
+@pytest.mark.parametrize("n,d,p0,bs", [(1, 8, 0, 16), (64, 128, 32, 32), (1000, 64, 48, 16),
+                                       (20011, 128, 96, 32), (136000, 128, 0, 32), (5000, 256, 224, 32),
+                                       (3000, 1024, 512, 32)])
+def test_tcgen05_gramian(n, d, p0, bs):
+    """tcgen05 Gramian (BF16 hi/lo, FP32 accumulate) against FP64 numpy."""
+    import torch
+    if d < p0 + bs:
+        pytest.skip("block outside d")
+    rng = np.random.default_rng(n)
+    X = rng.normal(0, 0.3, (n, d)).astype(np.float32)
+    G = torch.full((d, bs), float("nan"), dtype=torch.float32, device="cuda")
+    _abi.ials_partial_gramian_bf16(torch.from_numpy(X).cuda(), n, d, p0, bs, G)
+    ref = X.astype(np.float64).T @ X[:, p0:p0 + bs].astype(np.float64)
+    got = G.cpu().numpy()
+    err = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-30)
+    assert err <= 1e-4, err
