@@ -204,6 +204,44 @@ ials_status ials_partial_gramian_bf16(const float *X, int64_t n, int32_t d, int3
 ials_status ials_partial_gramian_noalloc(const float *X, int64_t n, int32_t d, int32_t p0,
                                          int32_t bs, float *G, void *cuda_stream);
 
+/* --- fold-in serving ----------------------------------------------------
+ * New users are solved against frozen item factors, as the evaluation protocol
+ * of Section 5.1.1 does for held-out users.  The paper gives no procedure;
+ * this library starts from w = 0 and runs `sweeps` passes of the user-side
+ * block steps of Algorithm 3 with H and G^I = H^T H fixed and
+ * lambda_u = lambda (1 + nu n).  One sweep with b = d is Eq. 3.
+ *
+ * ials_foldin_open copies H (n_items x d, host or device) to the device,
+ * forms G^I, and reserves workspace_bytes of device memory for requests.
+ * params->d and params->b (16, 32, 64 or 128, dividing d), alpha0, lambda, nu
+ * apply; precision and flags are ignored (FP32).  cuda_stream is used for the
+ * set-up only.  A scheduler thread batches requests continuously: queued
+ * requests are admitted in arrival order whenever their device memory fits the
+ * free workspace and one of four stream slots is free, so new requests start
+ * while earlier ones are still running.  A request's result does not depend on
+ * the requests it is batched with. */
+ials_status ials_foldin_open(const float *H, int32_t n_items, const ials_params *params,
+                             size_t workspace_bytes, int32_t sweeps, void *cuda_stream,
+                             ials_srv **out);
+
+/* Queue one request: n item ids (host array, each in [0, n_items)) and
+ * optional labels y (host array, NULL = all ones; weights are 1).  Thread-safe.
+ * Returns IALS_EAGAIN if the queue is full and IALS_EINVAL if the request can
+ * never fit the workspace.  *ticket identifies the request for poll. */
+ials_status ials_foldin_submit(ials_srv *srv, const int32_t *items, const float *y, int32_t n,
+                               uint64_t *ticket);
+
+/* Wait up to timeout_us microseconds (<= 0: do not wait) for a request.  On
+ * IALS_OK, w_out (host, d floats) receives the embedding and the ticket is
+ * released.  IALS_EAGAIN: not ready (timeout_us <= 0); IALS_ETIMEDOUT: not ready
+ * within timeout_us; IALS_ENOTFOUND: unknown or already collected ticket;
+ * IALS_ENOTPD: a block Hessian was not positive definite (ticket released).
+ * Thread-safe. */
+ials_status ials_foldin_poll(ials_srv *srv, uint64_t ticket, float *w_out, int32_t timeout_us);
+
+/* Stop the scheduler, drop queued requests and release everything (NULL: no-op). */
+ials_status ials_foldin_close(ials_srv *srv);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *ials_last_error(void);
 

@@ -12,12 +12,13 @@ import numpy as np
 
 from . import _abi
 from ._abi import (IalsError, ials_block_step, ials_create, ials_destroy, ials_epoch,
+                   ials_foldin_close, ials_foldin_open, ials_foldin_poll, ials_foldin_submit,
                    ials_get_factors, ials_get_residuals, ials_last_error, ials_last_stats,
                    ials_objective, ials_partial_gramian, ials_recompute_residuals,
                    ials_set_factors, make_params)
 
 __all__ = [
-    "Model", "IalsError", "make_params", "ials_create", "ials_destroy", "ials_epoch",
+    "Model", "FoldinServer", "IalsError", "make_params", "ials_create", "ials_destroy", "ials_epoch",
     "ials_objective", "ials_get_factors", "ials_set_factors", "ials_recompute_residuals",
     "ials_block_step", "ials_get_residuals", "ials_last_stats", "ials_partial_gramian",
     "ials_last_error",
@@ -91,3 +92,43 @@ class Model:
 
     def stats(self):
         return ials_last_stats(self.ctx)
+
+
+class FoldinServer:
+    """Fold-in of new users against frozen item factors (continuous batching).
+
+    ``submit`` queues a request and returns a ticket; ``result`` waits for it.
+    """
+
+    def __init__(self, H, d, b, alpha0, lam, nu=0.0, sweeps=4, workspace_bytes=1 << 30,
+                 stream=None):
+        H = np.ascontiguousarray(H, dtype=np.float32)
+        self.d = d
+        self.params = make_params(d, b, alpha0, lam, nu)
+        self.srv = ials_foldin_open(H, H.shape[0], self.params, workspace_bytes, sweeps, stream)
+
+    def submit(self, items, y=None):
+        return ials_foldin_submit(self.srv, items, y)
+
+    def poll(self, ticket, timeout_us=0):
+        """(status, w): status 0 with the embedding, or EAGAIN / ETIMEDOUT with None."""
+        w = np.empty(self.d, np.float32)
+        st = ials_foldin_poll(self.srv, ticket, w, timeout_us)
+        return st, (w if st in (_abi.OK, _abi.ENOTPD) else None)
+
+    def result(self, ticket, timeout_s=60.0):
+        st, w = self.poll(ticket, int(timeout_s * 1e6))
+        if st != _abi.OK:
+            raise IalsError(st, ials_last_error())
+        return w
+
+    def close(self):
+        if getattr(self, "srv", None) is not None:
+            ials_foldin_close(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

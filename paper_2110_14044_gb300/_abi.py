@@ -29,6 +29,7 @@ EXPORTS = (
     "ials_set_factors", "ials_recompute_residuals", "ials_block_step", "ials_get_residuals",
     "ials_last_stats", "ials_partial_gramian", "ials_last_error", "ials_profile_epochs",
     "ials_work_model", "ials_partial_gramian_noalloc", "ials_partial_gramian_bf16",
+    "ials_foldin_open", "ials_foldin_submit", "ials_foldin_poll", "ials_foldin_close",
 )
 
 KERNEL_KINDS = ("residual", "gram", "rowterm", "sparse", "split_solve", "split_resid", "retry",
@@ -77,6 +78,10 @@ def lib():
             "ials_work_model": ([vp, vp, vp, i32], st),
             "ials_partial_gramian_noalloc": ([vp, i64, i32, i32, i32, vp, vp], st),
             "ials_partial_gramian_bf16": ([vp, i64, i32, i32, i32, vp, vp], st),
+            "ials_foldin_open": ([vp, i32, P, C.c_size_t, i32, vp, C.POINTER(vp)], st),
+            "ials_foldin_submit": ([vp, vp, vp, i32, C.POINTER(C.c_uint64)], st),
+            "ials_foldin_poll": ([vp, C.c_uint64, vp, i32], st),
+            "ials_foldin_close": ([vp], st),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -214,3 +219,31 @@ def ials_partial_gramian_bf16(X, n, d, p0, bs, G, stream=None):
     """Partial Gramian on tcgen05 tensor cores (BF16 hi/lo compensated, FP32 accumulate)."""
     return _check(lib().ials_partial_gramian_bf16(_ptr(X), int(n), int(d), int(p0), int(bs), _ptr(G),
                                                   _stream(stream)))
+
+
+def ials_foldin_open(H, n_items, params, workspace_bytes, sweeps, stream=None):
+    out = C.c_void_p()
+    _check(lib().ials_foldin_open(_ptr(H), int(n_items), C.byref(params), int(workspace_bytes),
+                                  int(sweeps), _stream(stream), C.byref(out)))
+    return out
+
+
+def ials_foldin_submit(srv, items, y=None):
+    """Queue one request (numpy int32 items, optional float32 y); returns a ticket."""
+    items = np.ascontiguousarray(items, dtype=np.int32)
+    y = None if y is None else np.ascontiguousarray(y, dtype=np.float32)
+    t = C.c_uint64(0)
+    _check(lib().ials_foldin_submit(srv, _ptr(items), _ptr(y), int(items.size), C.byref(t)))
+    return t.value
+
+
+def ials_foldin_poll(srv, ticket, w_out, timeout_us=0):
+    """Status of one request; on OK w_out (float32 numpy, d) holds the embedding."""
+    status = lib().ials_foldin_poll(srv, C.c_uint64(ticket), _ptr(w_out), int(timeout_us))
+    if status not in (OK, EAGAIN, ETIMEDOUT, ENOTPD):
+        _check(status)
+    return status
+
+
+def ials_foldin_close(srv):
+    return _check(lib().ials_foldin_close(srv))

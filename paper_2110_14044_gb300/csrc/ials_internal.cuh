@@ -107,6 +107,24 @@ struct StepArgs {
     Profiler *prof;         // host only: event marks around launches, or nullptr
 };
 
+// One fold-in request inside the server's workspace arena (byte offsets; the
+// items start at arena + off, the others are relative to that).
+struct FoldReq {
+    int64_t off, y_off, e_off, l_off, w_off;
+    int32_t n, has_y;
+};
+
+struct FoldArgs {
+    const FoldReq *req;
+    int32_t n_req;
+    uint8_t *arena;
+    const float *H;   // frozen item factors, n_items x d
+    const float *G;   // G^I = H^T H, d x d
+    int32_t d, b, sweeps;
+    float alpha0, lambda, nu;
+    int32_t *status;  // per request: 0 ok, 4 not positive definite
+};
+
 // ---------------------------------------------------------------- launchers
 // dense kernels (k_dense.cu)
 cudaError_t launch_residual(const int64_t *u_ptr, const int32_t *u_idx, const float *W,
@@ -178,6 +196,9 @@ cudaError_t launch_sparse_b32(const StepArgs &a, cudaStream_t s);
 // block sizes 64 and 128 (k_sparse_b64.cu, k_sparse_b128.cu): one CTA per task
 cudaError_t launch_sparse_b64(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_sparse_b128(const StepArgs &a, cudaStream_t s);
+// fold-in (k_foldin.cu): one CTA per request; factors per request: foldin_factor_floats
+cudaError_t launch_foldin(const FoldArgs &a, cudaStream_t s);
+int64_t foldin_factor_floats(int32_t d, int32_t b);
 // BF16 mode (k_sparse_bf16.cu): tensor-core statistics for block sizes 16 and 32
 cudaError_t launch_sparse_bf16_b16(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_sparse_bf16_b32(const StepArgs &a, cudaStream_t s);
