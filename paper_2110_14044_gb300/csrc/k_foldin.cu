@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) k_foldin(FoldArgs a) {
             for (int k = 0; k < nb; ++k) {
                 const int p0 = k * B;
                 // gradient: thread (g, j) with j < B, g < nt / B sums a strided share
-                const int gsz = nt / B;
+                const int gsz = nt / B < 8 ? nt / B : 8;  // gp holds 8 partial rows
                 const int j = tid % B, g = tid / B;
                 if (g < gsz) {
                     float t = 0.f;
