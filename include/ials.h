@@ -239,6 +239,12 @@ ials_status ials_foldin_submit(ials_srv *srv, const int32_t *items, const float 
  * Thread-safe. */
 ials_status ials_foldin_poll(ials_srv *srv, uint64_t ticket, float *w_out, int32_t timeout_us);
 
+/* ials_foldin_poll that also returns, in *latency_us (if non-NULL), the time
+ * from the request's submission to the moment its result reached host memory,
+ * both taken by the library with a monotonic clock. */
+ials_status ials_foldin_poll_timed(ials_srv *srv, uint64_t ticket, float *w_out, int32_t timeout_us,
+                                   double *latency_us);
+
 /* Stop the scheduler, drop queued requests and release everything (NULL: no-op). */
 ials_status ials_foldin_close(ials_srv *srv);
 

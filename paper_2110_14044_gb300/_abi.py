@@ -30,6 +30,7 @@ EXPORTS = (
     "ials_last_stats", "ials_partial_gramian", "ials_last_error", "ials_profile_epochs",
     "ials_work_model", "ials_partial_gramian_noalloc", "ials_partial_gramian_bf16",
     "ials_foldin_open", "ials_foldin_submit", "ials_foldin_poll", "ials_foldin_close",
+    "ials_foldin_poll_timed",
 )
 
 KERNEL_KINDS = ("residual", "gram", "rowterm", "sparse", "split_solve", "split_resid", "retry",
@@ -82,6 +83,7 @@ def lib():
             "ials_foldin_submit": ([vp, vp, vp, i32, C.POINTER(C.c_uint64)], st),
             "ials_foldin_poll": ([vp, C.c_uint64, vp, i32], st),
             "ials_foldin_close": ([vp], st),
+            "ials_foldin_poll_timed": ([vp, C.c_uint64, vp, i32, C.POINTER(C.c_double)], st),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -247,3 +249,13 @@ def ials_foldin_poll(srv, ticket, w_out, timeout_us=0):
 
 def ials_foldin_close(srv):
     return _check(lib().ials_foldin_close(srv))
+
+
+def ials_foldin_poll_timed(srv, ticket, w_out, timeout_us=0):
+    """(status, latency in microseconds from submit to result, or None)."""
+    lat = C.c_double(-1.0)
+    status = lib().ials_foldin_poll_timed(srv, C.c_uint64(ticket), _ptr(w_out), int(timeout_us),
+                                          C.byref(lat))
+    if status not in (OK, EAGAIN, ETIMEDOUT, ENOTPD):
+        _check(status)
+    return status, (lat.value if status in (OK, ENOTPD) else None)

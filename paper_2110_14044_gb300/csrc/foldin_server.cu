@@ -50,6 +50,7 @@ ials_status sfail(ials_status st, const std::string &msg) {
 
 struct Request {
     uint64_t ticket = 0;
+    std::chrono::steady_clock::time_point t_submit, t_done;
     std::vector<int32_t> items;
     std::vector<float> y;
     bool has_y = false;
@@ -136,7 +137,9 @@ struct ials_srv {
     }
 
     void retire(Slot &s) {
+        const auto now = std::chrono::steady_clock::now();
         for (size_t i = 0; i < s.reqs.size(); ++i) {
+            s.reqs[i]->t_done = now;
             Request &r = *s.reqs[i];
             r.w.assign(s.h_out + i * d, s.h_out + (i + 1) * d);
             r.status = s.h_st[i];
@@ -404,6 +407,7 @@ ials_status ials_foldin_submit(ials_srv *s, const int32_t *items, const float *y
         std::lock_guard<std::mutex> g(s->mu);
         if (s->pending.size() >= kMaxPending) return sfail(IALS_EAGAIN, "fold-in queue full");
         r->ticket = s->next_ticket++;
+        r->t_submit = std::chrono::steady_clock::now();
         s->table[r->ticket] = r;
         s->pending.push_back(r);
         *ticket = r->ticket;
@@ -412,7 +416,8 @@ ials_status ials_foldin_submit(ials_srv *s, const int32_t *items, const float *y
     return IALS_OK;
 }
 
-ials_status ials_foldin_poll(ials_srv *s, uint64_t ticket, float *w_out, int32_t timeout_us) {
+ials_status ials_foldin_poll_timed(ials_srv *s, uint64_t ticket, float *w_out, int32_t timeout_us,
+                                   double *latency_us) {
     if (!s || !w_out) return sfail(IALS_EINVAL, "bad poll arguments");
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->table.find(ticket);
@@ -422,11 +427,17 @@ ials_status ials_foldin_poll(ials_srv *s, uint64_t ticket, float *w_out, int32_t
         s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return r->done; });
     if (!r->done) return timeout_us > 0 ? sfail(IALS_ETIMEDOUT, "result not ready") : IALS_EAGAIN;
     std::memcpy(w_out, r->w.data(), sizeof(float) * (size_t)s->d);
+    if (latency_us)
+        *latency_us = std::chrono::duration<double, std::micro>(r->t_done - r->t_submit).count();
     const int st = r->status;
     s->table.erase(it);
     if (st == 4) return sfail(IALS_ENOTPD, "a block Hessian was not positive definite");
     if (st != 0) return sfail((ials_status)st, "fold-in failed");
     return IALS_OK;
+}
+
+ials_status ials_foldin_poll(ials_srv *s, uint64_t ticket, float *w_out, int32_t timeout_us) {
+    return ials_foldin_poll_timed(s, ticket, w_out, timeout_us, nullptr);
 }
 
 ials_status ials_foldin_close(ials_srv *s) {
