@@ -335,6 +335,14 @@ def run_ours(args):
         m2.close()
     if rank == 0 and args.foldin:
         line["foldin"] = run_foldin()
+    if rank == 0 and args.autotune:
+        from paper_2110_14044_gb300 import autotune
+        tuned = {}
+        for name, pr in (("fp32", _abi.PREC_FP32), ("bf16", _abi.PREC_BF16)):
+            best, table = autotune.autotune_block_size(data, prob.d, prob.alpha0, prob.lam, prob.nu,
+                                                       precision=pr, W0=prob.W0, H0=prob.H0)
+            tuned[name] = {"best_b": best, "epoch_s_by_b": {str(k): v for k, v in table.items()}}
+        line["autotune"] = tuned
     if rank == 0:
         print(json.dumps(line), flush=True)
     m.close()
@@ -456,6 +464,8 @@ def main():
                     help="do not also time the other precision")
     ap.add_argument("--no-foldin", dest="foldin", action="store_false",
                     help="do not run the fold-in serving measurement")
+    ap.add_argument("--autotune", action="store_true",
+                    help="also time every admissible block size per precision (b sweep)")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-step", action="store_true",

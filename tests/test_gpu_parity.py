@@ -412,3 +412,15 @@ def test_large_block_fp64_retry_path():
     Wa, Ha = a.factors()
     Wb, Hb = b.factors()
     assert rel_embed_err(Wb, Wa) <= STEP_TOL and rel_embed_err(Hb, Ha) <= STEP_TOL
+
+
+def test_autotuner_returns_the_fastest_admissible_block():
+    from paper_2110_14044_gb300 import autotune
+    prob = small(d=64, seed=60)
+    best, table = autotune.autotune_block_size(prob.data, 64, 0.1, 1e-3, 0.0, epochs=1,
+                                               W0=prob.W0, H0=prob.H0)
+    assert set(table) == {8, 16, 32, 64}
+    assert best == min(table, key=table.get) and all(v > 0 for v in table.values())
+    best16, t16 = autotune.autotune_block_size(prob.data, 64, 0.1, 1e-3, 0.0, epochs=1,
+                                               precision=_abi.PREC_BF16, W0=prob.W0, H0=prob.H0)
+    assert set(t16) == {16, 32}
