@@ -131,6 +131,8 @@ struct ials_ctx {
     float *W = nullptr, *H = nullptr, *e = nullptr, *y = nullptr, *alpha = nullptr;
     __nv_bfloat16 *Wh = nullptr, *Wl = nullptr, *Hh = nullptr, *Hl = nullptr;  // BF16 mode shadows
     GramMaps maps[2];          // BF16 mode: tensor maps of the W (0) and H (1) shadows
+    RowMaps rmaps[2];          // BF16 mode: row-term maps of the users (0) and items (1) side
+    __nv_bfloat16 *gth = nullptr, *gtl = nullptr;  // BF16 mode: G^T hi/lo (b x d)
     int32_t *dev_err = nullptr;  // nonzero if a bounded device wait gave up
     SideDev side[2];
     float *G = nullptr, *gram_ws = nullptr, *R = nullptr, *part = nullptr, *delta = nullptr;
@@ -237,9 +239,15 @@ ials_status step_enqueue(ials_ctx *c, int side, int block, Profiler *prof = null
         IALS_CUDA(launch_gram(F, n_fixed, d, p0, b, c->G, c->gram_ws, s), "partial Gramian");
     }
     prof_mark(prof, K_ROWTERM, s);
-    IALS_CUDA(launch_rowterm(X, sd.ptr, sd.n_rows, d, p0, b, c->G, (float)c->p.alpha0,
-                             (float)c->p.lambda, (float)c->p.nu, c->R, s),
-              "row terms");
+    if (c->p.precision == IALS_PREC_BF16) {
+        IALS_CUDA(launch_rowterm_tc(c->rmaps[side], c->G, c->gth, c->gtl, X, sd.ptr, sd.n_rows, d, p0, b,
+                                    (float)c->p.alpha0, (float)c->p.lambda, (float)c->p.nu, c->R, c->dev_err, s),
+                  "row terms (tcgen05)");
+    } else {
+        IALS_CUDA(launch_rowterm(X, sd.ptr, sd.n_rows, d, p0, b, c->G, (float)c->p.alpha0,
+                                 (float)c->p.lambda, (float)c->p.nu, c->R, s),
+                  "row terms");
+    }
     prof_mark(prof, -1, s);
     IALS_CUDA(cudaMemsetAsync(c->ctl, 0, 2 * sizeof(int32_t), s), "counter reset");
     StepArgs a;
@@ -471,6 +479,8 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
         ALLOC(c->Wl, (int64_t)n_users * d, "W lo");
         ALLOC(c->Hh, (int64_t)n_items * d, "H hi");
         ALLOC(c->Hl, (int64_t)n_items * d, "H lo");
+        ALLOC(c->gth, (int64_t)b * d, "G^T hi");
+        ALLOC(c->gtl, (int64_t)b * d, "G^T lo");
     }
     ALLOC(c->e, nnz, "residuals");
     if (y) ALLOC(c->y, nnz, "y");
@@ -536,7 +546,9 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->dev_err, 0, sizeof(int32_t), c->stream);
     if (e3 == cudaSuccess && c->Wh &&
         (!make_gram_maps(c->maps[0], c->Wh, c->Wl, n_users, d, b) ||
-         !make_gram_maps(c->maps[1], c->Hh, c->Hl, n_items, d, b))) {
+         !make_gram_maps(c->maps[1], c->Hh, c->Hl, n_items, d, b) ||
+         !make_row_maps(c->rmaps[0], c->Wh, c->Wl, n_users, d, c->gth, c->gtl, b) ||
+         !make_row_maps(c->rmaps[1], c->Hh, c->Hl, n_items, d, c->gth, c->gtl, b))) {
         delete c;
         return fail(IALS_ECUDA, "could not encode TMA tensor maps (cuTensorMapEncodeTiled)");
     }

@@ -171,6 +171,16 @@ struct alignas(64) GramMaps {
 bool make_gram_maps(GramMaps &g, const __nv_bfloat16 *hi, const __nv_bfloat16 *lo, int64_t rows, int32_t d,
                     int32_t b);
 int64_t gram_tc_ws_floats(int64_t n, int32_t d, int32_t bs);
+// tcgen05 row terms: tensor maps of the updated side's hi/lo shadows (K-major
+// boxes of 64 x 128) and of G^T hi/lo (b x d); the launcher first writes G^T.
+struct alignas(64) RowMaps {
+    unsigned char xh[128], xl[128], gh[128], gl[128];
+};
+bool make_row_maps(RowMaps &m, const __nv_bfloat16 *xh, const __nv_bfloat16 *xl, int64_t rows, int32_t d,
+                   const __nv_bfloat16 *gth, const __nv_bfloat16 *gtl, int32_t b);
+cudaError_t launch_rowterm_tc(const RowMaps &m, const float *G, __nv_bfloat16 *gth, __nv_bfloat16 *gtl,
+                              const float *X, const int64_t *ptr, int32_t n_rows, int32_t d, int32_t p0, int32_t b,
+                              float alpha0, float lambda, float nu, float *R, int32_t *err, cudaStream_t s);
 cudaError_t launch_gram_tc(const GramMaps &g, int64_t n, int32_t d, int32_t p0, int32_t bs, float *G, float *ws,
                            int32_t *err, cudaStream_t s);
 

@@ -220,6 +220,155 @@ __global__ void __launch_bounds__(128, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;\n" ::"r"(tmem) : "memory");
 }
 
+// ------------------------------------------------------------------ row terms
+// R[r, f] = alpha0 * sum_k X[r, k] G[k, f] + lambda (1 + nu n_r) X[r, p0 + f]
+// (Algorithm 3 gradient initialisation; dense part of Eq. 11) on tcgen05:
+// D (128 rows x N) = A (rows x d) B^T with A[m][k] = X[r0+m][k] and
+// B[f][k] = G[k][f] = G^T[f][k].  Both operands are K-major (X rows and the rows
+// of G^T are contiguous in k): TMA boxes of 64 k x 128 rows (A) and 64 k x N
+// rows (B) with the 128B swizzle, i.e. atoms of 8 rows x 128 B, stride byte
+// offset 1024 between atoms; a K step of 16 advances the start address by 32 B
+// inside the atom.  hi/lo compensation as in the Gramian.
+template <int N>
+struct TcRowCfg {
+    static constexpr int A_BYTES = 128 * 64 * 2;   // 16 KB
+    static constexpr int B_BYTES = N * 64 * 2;
+    static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    static constexpr int STAGES = 2;
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+};
+
+constexpr uint32_t idesc_bf16_k(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int N>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_rowterm(const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
+                 const __grid_constant__ CUtensorMap mGh, const __grid_constant__ CUtensorMap mGl,
+                 const float *__restrict__ X, const int64_t *__restrict__ ptr, int32_t n_rows, int32_t d,
+                 int32_t p0, float alpha0, float lambda, float nu, float *__restrict__ R, int32_t *err) {
+    using C = TcRowCfg<N>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + C::STAGES * C::STAGE);
+    uint64_t *empty = full + C::STAGES;
+    uint64_t *done = empty + C::STAGES;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int r0 = blockIdx.x * 128;
+    const int nk = d / 64 + (d % 64 ? 1 : 0);
+    if (tid == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;\n" ::"r"(smem_u32(tslot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    if (tid == 0) {
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % C::STAGES;
+            if (kt >= C::STAGES && !mbar_wait(&empty[s], ((kt / C::STAGES) - 1) & 1)) {
+                atomicExch(err, 11);
+                break;
+            }
+            uint8_t *st = base + s * C::STAGE;
+            mbar_expect_tx(&full[s], C::STAGE);
+            tma_load_2d(st, &mXh, kt * 64, r0, &full[s]);
+            tma_load_2d(st + C::A_BYTES, &mXl, kt * 64, r0, &full[s]);
+            tma_load_2d(st + 2 * C::A_BYTES, &mGh, kt * 64, 0, &full[s]);
+            tma_load_2d(st + 2 * C::A_BYTES + C::B_BYTES, &mGl, kt * 64, 0, &full[s]);
+        }
+    } else if (tid == 32) {
+        constexpr uint32_t idesc = idesc_bf16_k(128, N);
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % C::STAGES;
+            if (!mbar_wait(&full[s], (kt / C::STAGES) & 1)) {
+                atomicExch(err, 12);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t xh = smem_u32(base + s * C::STAGE), xl = xh + C::A_BYTES;
+            const uint32_t gh = xh + 2 * C::A_BYTES, gl = gh + C::B_BYTES;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint64_t dxh = smem_desc(xh + 32 * j, 16, 1024, SWZ_128B);
+                const uint64_t dxl = smem_desc(xl + 32 * j, 16, 1024, SWZ_128B);
+                const uint64_t dgh = smem_desc(gh + 32 * j, 16, 1024, SWZ_128B);
+                const uint64_t dgl = smem_desc(gl + 32 * j, 16, 1024, SWZ_128B);
+                const uint32_t acc = (kt > 0 || j > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p, q;\n setp.ne.b32 p, %4, 0;\n setp.eq.b32 q, %4, %4;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %5, %3, q;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %6, %2, %3, q;\n}\n" ::"r"(tmem),
+                    "l"(dxh), "l"(dgh), "r"(idesc), "r"(acc), "l"(dgl), "l"(dxl)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(&empty[s]))
+                         : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         smem_u32(done))
+                     : "memory");
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(done, 0);
+    if (!ok && (tid & 31) == 0) atomicExch(err, 13);
+    tc_fence_after();
+    uint32_t r[32];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+    const int row = r0 + warp * 32 + (tid & 31);
+    if (row < n_rows && ok) {
+        const float lam = lambda * (1.0f + nu * (float)(ptr[row + 1] - ptr[row]));
+        const float *x = X + (int64_t)row * d + p0;
+        float *out = R + (int64_t)row * N;
+#pragma unroll
+        for (int f = 0; f < N; f += 4) {
+            const float4 xv = *reinterpret_cast<const float4 *>(x + f);
+            *reinterpret_cast<float4 *>(out + f) =
+                make_float4(alpha0 * __uint_as_float(r[f]) + lam * xv.x, alpha0 * __uint_as_float(r[f + 1]) + lam * xv.y,
+                            alpha0 * __uint_as_float(r[f + 2]) + lam * xv.z, alpha0 * __uint_as_float(r[f + 3]) + lam * xv.w);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;\n" ::"r"(tmem) : "memory");
+}
+
+// G (d x b, FP32) -> G^T hi and lo (b x d, BF16)
+__global__ void k_transpose_split(const float *__restrict__ G, int32_t d, int32_t b, __nv_bfloat16 *__restrict__ th,
+                                  __nv_bfloat16 *__restrict__ tl) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d * b) return;
+    const int f = i / d, k = i % d;
+    const float x = G[(int64_t)k * b + f];
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    th[i] = h;
+    tl[i] = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
 // ------------------------------------------------------------------ host side
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -278,6 +427,51 @@ bool make_gram_maps(GramMaps &g, const __nv_bfloat16 *hi, const __nv_bfloat16 *l
            encode_2d(reinterpret_cast<CUtensorMap *>(g.al), lo, rows, d, 64, TC_BK, CU_TENSOR_MAP_SWIZZLE_128B) &&
            encode_2d(reinterpret_cast<CUtensorMap *>(g.bh), hi, rows, d, b, TC_BK, bsw) &&
            encode_2d(reinterpret_cast<CUtensorMap *>(g.bl), lo, rows, d, b, TC_BK, bsw);
+}
+
+bool make_row_maps(RowMaps &m, const __nv_bfloat16 *xh, const __nv_bfloat16 *xl, int64_t rows, int32_t d,
+                   const __nv_bfloat16 *gth, const __nv_bfloat16 *gtl, int32_t b) {
+    if (d % 8 != 0 || (b != 16 && b != 32)) return false;
+    static_assert(sizeof(CUtensorMap) == sizeof(m.xh), "tensor map size");
+    return encode_2d(reinterpret_cast<CUtensorMap *>(m.xh), xh, rows, d, 64, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+           encode_2d(reinterpret_cast<CUtensorMap *>(m.xl), xl, rows, d, 64, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+           encode_2d(reinterpret_cast<CUtensorMap *>(m.gh), gth, b, d, 64, b, CU_TENSOR_MAP_SWIZZLE_128B) &&
+           encode_2d(reinterpret_cast<CUtensorMap *>(m.gl), gtl, b, d, 64, b, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+cudaError_t launch_rowterm_tc(const RowMaps &m, const float *G, __nv_bfloat16 *gth, __nv_bfloat16 *gtl,
+                              const float *X, const int64_t *ptr, int32_t n_rows, int32_t d, int32_t p0, int32_t b,
+                              float alpha0, float lambda, float nu, float *R, int32_t *err, cudaStream_t s) {
+    if (n_rows == 0) return cudaSuccess;
+    k_transpose_split<<<(d * b + 255) / 256, 256, 0, s>>>(G, d, b, gth, gtl);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const CUtensorMap *xh = reinterpret_cast<const CUtensorMap *>(m.xh);
+    const CUtensorMap *xl = reinterpret_cast<const CUtensorMap *>(m.xl);
+    const CUtensorMap *gh = reinterpret_cast<const CUtensorMap *>(m.gh);
+    const CUtensorMap *gl = reinterpret_cast<const CUtensorMap *>(m.gl);
+    const int grid = (n_rows + 127) / 128;
+    static bool a16 = false, a32 = false;
+    if (b == 16) {
+        if (!a16) {
+            e = cudaFuncSetAttribute(k_tc_rowterm<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcRowCfg<16>::SMEM);
+            if (e != cudaSuccess) return e;
+            a16 = true;
+        }
+        k_tc_rowterm<16><<<grid, 128, TcRowCfg<16>::SMEM, s>>>(*xh, *xl, *gh, *gl, X, ptr, n_rows, d, p0, alpha0,
+                                                               lambda, nu, R, err);
+    } else if (b == 32) {
+        if (!a32) {
+            e = cudaFuncSetAttribute(k_tc_rowterm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcRowCfg<32>::SMEM);
+            if (e != cudaSuccess) return e;
+            a32 = true;
+        }
+        k_tc_rowterm<32><<<grid, 128, TcRowCfg<32>::SMEM, s>>>(*xh, *xl, *gh, *gl, X, ptr, n_rows, d, p0, alpha0,
+                                                               lambda, nu, R, err);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 int64_t gram_tc_ws_floats(int64_t n, int32_t d, int32_t bs) {
