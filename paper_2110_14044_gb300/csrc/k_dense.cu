@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(256) k_residual(const int64_t *__restrict__ u_
                                                   int32_t n_users, int32_t d,
                                                   float *__restrict__ e, double *__restrict__ part) {
     constexpr int SG = 1 << SGL, NSUB = 32 / SG;  // NSUB sub-groups, SG interactions each per chunk
-    constexpr int U = SG < 4 ? SG : 4;
+    constexpr int UMAX = MAXV >= 16 ? 1 : (MAXV >= 8 ? 2 : 4);  // keep U * MAXV float4 in registers <= 16
+    constexpr int U = SG < UMAX ? SG : UMAX;
     const int lane = threadIdx.x & 31;
     const int sub = lane >> SGL, sl = lane & (SG - 1);
     const int nv4 = d >> 2;
