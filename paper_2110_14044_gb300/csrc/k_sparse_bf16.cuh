@@ -231,14 +231,14 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
         }
         __syncwarp();
         float A[B];
-        float g = vv[col];
-        if (tk.slot >= 0) {  // a chunk of a long row: store the partial statistics (row col)
 #pragma unroll
-            for (int j = 0; j < B; j += 4) {
-                const float4 v = *reinterpret_cast<const float4 *>(As + col * SA + j);
-                A[j] = v.x; A[j + 1] = v.y; A[j + 2] = v.z; A[j + 3] = v.w;
-            }
-            __syncwarp();
+        for (int j = 0; j < B; j += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(As + col * SA + j);
+            A[j] = v.x; A[j + 1] = v.y; A[j + 2] = v.z; A[j + 3] = v.w;
+        }
+        float g = vv[col];
+        __syncwarp();
+        if (tk.slot >= 0) {  // a chunk of a long row: store the partial statistics (row col)
             if (sub == 0) {
                 float *P = a.part + (int64_t)tk.slot * (B * B + B);
 #pragma unroll
@@ -250,19 +250,11 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
         }
         const int row = tk.row;
         const float lam = a.lambda * (1.0f + a.nu * (float)tk.len);
-        if (sub == 0) As[col * SA + col] += lam;
-        __syncwarp();
 #pragma unroll
-        for (int j = 0; j < B; j += 4) {
-            const float4 v = *reinterpret_cast<const float4 *>(As + col * SA + j);
-            const float4 q = *reinterpret_cast<const float4 *>(sGpp + col * B + j);
-            A[j] = v.x + q.x; A[j + 1] = v.y + q.y; A[j + 2] = v.z + q.z; A[j + 3] = v.w + q.w;
-        }
-        const float diag0 = As[col * SA + col] + sGpp[col * B + col];
-        __syncwarp();
+        for (int j = 0; j < B; ++j) A[j] += sGpp[col * B + j] + (j == col ? lam : 0.f);
         g += a.R[(int64_t)row * B + col];
         float delta;
-        if (!chol_solve<B>(A, g, diag0, col, sub, w, a.force_fp64 != 0, delta)) {
+        if (!chol_solve<B>(A, g, col, sub, w, a.force_fp64 != 0, delta)) {
             queue_retry(a, lane, row);
             continue;
         }

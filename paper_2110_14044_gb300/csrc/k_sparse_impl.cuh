@@ -34,8 +34,7 @@ struct SparseCfg {
     static constexpr int CH = 32;                  // interactions staged per chunk
     static constexpr int VPAD = (B + 3) / 4 * 4;
     static constexpr int LSTR = B + 1;             // stride of the L factor copy
-    static constexpr int LREG = B * LSTR > 2 * (B + 4) ? B * LSTR : 2 * (B + 4);  // L copy / column buffers
-    static constexpr int WARP_FLOATS_RAW = CH * SB + 3 * CH + VPAD + LREG;
+    static constexpr int WARP_FLOATS_RAW = CH * SB + 3 * CH + VPAD + B * LSTR;
     static constexpr int WARP_FLOATS = (WARP_FLOATS_RAW + 3) / 4 * 4;
     static constexpr int GPP_FLOATS = (B * B + 3) / 4 * 4;
     static constexpr int WARPS = 8;
@@ -121,43 +120,46 @@ __device__ __forceinline__ void stage_chunk(const StepArgs &a, int64_t begin, in
 
 // Warp Cholesky solve A delta = g.  Lane l holds row col = l % B of the
 // symmetric matrix in A[] (entries right of the diagonal may hold anything
-// finite), entry col of g and diag0 = A[col][col].  Right-looking
-// factorisation, one column per step: the pivot is broadcast with a shuffle and
-// column k of L, together with z_k = g_k / L_kk of the forward substitution
-// L z = g, is exchanged through a double-buffered column in w.L, so each step
-// needs one __syncwarp.  Each lane keeps its own pivot; one vote at the end
-// rejects the solve if a pivot was not positive, not finite, or below 1e-5 of
-// its original diagonal (more than ~17 bits lost).  Returns false
-// (warp-uniform) on a bad pivot or a non-finite solution; on success `delta`
-// holds entry col of the solution.
+// finite) and entry col of g.  Right-looking factorisation, one column per
+// step: the pivot is broadcast with a shuffle and column k of L is exchanged
+// through a double-buffered column in w.L, so each step needs one __syncwarp.
+// Lane k checks its own pivot (positive, finite, and not below 1e-5 of its
+// original diagonal, i.e. no more than ~17 bits lost); one vote at the end
+// decides for the whole warp.  Returns false (warp-uniform) on a bad pivot or a
+// non-finite solution; on success `delta` holds entry col of the solution.
 template <int B>
-__device__ __forceinline__ bool chol_solve(float (&A)[B], float g, float diag0, int col, int sub,
+__device__ __forceinline__ bool chol_solve(float (&A)[B], float g, int col, int sub,
                                            const WarpSmem &w, bool force_fail, float &delta) {
-    constexpr int CB = B + 4;  // column buffer: B entries of L, then z_k
-    float inv_diag = 0.f, piv = 0.f;
-    float *cb = w.L;  // two column buffers while factorising
+    float diag0 = 0.f;
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+        if (j == col) diag0 = A[j];
+    bool bad = force_fail;
+    float inv_diag = 0.f;
+    float *cb = w.L;  // two column buffers of B floats while factorising
 #pragma unroll
     for (int k = 0; k < B; ++k) {
+        if (col == k) bad = bad || !(A[k] > 1e-5f * diag0) || !(A[k] <= 3.0e38f);
         const float akk = __shfl_sync(kFull, A[k], k);
         const float inv = rsqrtf(fmaxf(akk, 1e-30f));
         const float lck = A[k] * inv;
-        float *v = cb + (k & 1) * CB;
-        if (col == k) {
-            inv_diag = inv;
-            piv = akk;
-            if (sub == 0) v[B] = g * inv;
-        }
+        if (col == k) inv_diag = inv;
         A[k] = lck;
+        float *v = cb + (k & 1) * B;
         if (sub == 0) v[col] = lck;
         __syncwarp();
-        const float zk = v[B];
-        if (col == k) g = zk;
-        else if (col > k) g -= lck * zk;
 #pragma unroll
         for (int j = k + 1; j < B; ++j) A[j] -= lck * v[j];
     }
-    const bool bad = force_fail || !(piv > 1e-5f * diag0) || !(piv <= 3.0e38f);
     if (__any_sync(kFull, bad)) return false;
+    // forward: L z = g
+    float z = g;
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+        const float zk = __shfl_sync(kFull, z * inv_diag, k);
+        if (col > k) z -= A[k] * zk;
+        else if (col == k) z = zk;
+    }
     // backward: L^T x = z, with the rows of L copied to shared memory
     __syncwarp();
     if (sub == 0) {
@@ -166,7 +168,7 @@ __device__ __forceinline__ bool chol_solve(float (&A)[B], float g, float diag0, 
             if (j <= col) w.L[col * SparseCfg<B>::LSTR + j] = A[j];
     }
     __syncwarp();
-    float x = g;
+    float x = z;
 #pragma unroll
     for (int k = B - 1; k >= 0; --k) {
         const float xk = __shfl_sync(kFull, x * inv_diag, k);
@@ -175,16 +177,6 @@ __device__ __forceinline__ bool chol_solve(float (&A)[B], float g, float diag0, 
     }
     delta = x;
     return __all_sync(kFull, isfinite(x));
-}
-
-// Entry col of a register array (select chain; used where the matrix is not in shared memory).
-template <int B>
-__device__ __forceinline__ float reg_at(const float (&A)[B], int col) {
-    float v = 0.f;
-#pragma unroll
-    for (int j = 0; j < B; ++j)
-        if (j == col) v = A[j];
-    return v;
 }
 
 template <int B>
@@ -279,7 +271,7 @@ __global__ void __launch_bounds__(256, 2) k_sparse(const StepArgs a) {
         for (int j = 0; j < B; ++j) acc[j] += sGpp[j * B + col] + (j == col ? lam : 0.f);
         g += a.R[(int64_t)row * B + col];
         float delta;
-        if (!chol_solve<B>(acc, g, reg_at<B>(acc, col), col, sub, w, a.force_fp64 != 0, delta)) {
+        if (!chol_solve<B>(acc, g, col, sub, w, a.force_fp64 != 0, delta)) {
             queue_retry(a, lane, row);
             continue;
         }
@@ -496,14 +488,14 @@ __global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
             __syncwarp();
         }
         float A[B];
-        float g = gs[col];
-        if (tk.slot >= 0) {  // a chunk of a long row: store the partial statistics (row col)
 #pragma unroll
-            for (int j = 0; j < B; j += 4) {
-                const float4 v = *reinterpret_cast<const float4 *>(As + col * SB + j);
-                A[j] = v.x; A[j + 1] = v.y; A[j + 2] = v.z; A[j + 3] = v.w;
-            }
-            __syncwarp();
+        for (int j = 0; j < B; j += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(As + col * SB + j);
+            A[j] = v.x; A[j + 1] = v.y; A[j + 2] = v.z; A[j + 3] = v.w;
+        }
+        float g = gs[col];
+        __syncwarp();
+        if (tk.slot >= 0) {  // a chunk of a long row: store the partial statistics (row col)
             if (sub == 0) {
                 float *P = a.part + (int64_t)tk.slot * (B * B + B);
 #pragma unroll
@@ -515,19 +507,11 @@ __global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
         }
         const int row = tk.row;
         const float lam = a.lambda * (1.0f + a.nu * (float)tk.len);
-        if (sub == 0) As[col * SB + col] += lam;
-        __syncwarp();
 #pragma unroll
-        for (int j = 0; j < B; j += 4) {
-            const float4 v = *reinterpret_cast<const float4 *>(As + col * SB + j);
-            const float4 q = *reinterpret_cast<const float4 *>(sGpp + col * B + j);
-            A[j] = v.x + q.x; A[j + 1] = v.y + q.y; A[j + 2] = v.z + q.z; A[j + 3] = v.w + q.w;
-        }
-        const float diag0 = As[col * SB + col] + sGpp[col * B + col];
-        __syncwarp();
+        for (int j = 0; j < B; ++j) A[j] += sGpp[col * B + j] + (j == col ? lam : 0.f);
         g += a.R[(int64_t)row * B + col];
         float delta;
-        if (!chol_solve<B>(A, g, diag0, col, sub, w, a.force_fp64 != 0, delta)) {
+        if (!chol_solve<B>(A, g, col, sub, w, a.force_fp64 != 0, delta)) {
             queue_retry(a, lane, row);
             continue;
         }
@@ -608,7 +592,7 @@ __global__ void __launch_bounds__(256) k_split_solve(const StepArgs a) {
                 acc[j] += a.alpha0 * a.G[(int64_t)(a.p0 + j) * B + col] + (j == col ? lam : 0.f);
             g += a.R[(int64_t)sr.row * B + col];
             float delta = 0.f;
-            const bool ok = chol_solve<B>(acc, g, reg_at<B>(acc, col), col, sub, w, a.force_fp64 != 0, delta);
+            const bool ok = chol_solve<B>(acc, g, col, sub, w, a.force_fp64 != 0, delta);
             if (!ok) {
                 queue_retry(a, lane, sr.row);
                 delta = 0.f;  // k_split_resid leaves the row's residuals alone
@@ -623,7 +607,7 @@ __global__ void __launch_bounds__(256) k_split_solve(const StepArgs a) {
 
 template <int B>
 constexpr int split_solve_smem() {
-    return ((B * B + B + 3) / 4 * 4 + (B + 3) / 4 * 4 + SparseCfg<B>::LREG) * 4;
+    return ((B * B + B + 3) / 4 * 4 + (B + 3) / 4 * 4 + B * (B + 1)) * 4;
 }
 
 // One warp per chunk of a split row: e_s -= <delta_row, f_{c_s,pi}>.
