@@ -14,8 +14,10 @@
 // applied) and are gathered with cp.async into two staging buffers.  One
 // ldmatrix.x4.trans of a 16 x 16 block serves both as the A fragment of an
 // m-tile and as the B fragments of the two matching n-tiles.  The Newton solve
-// (warp Cholesky, FP32), apply and the FP32 residual update (x = hi + lo) are
-// those of the FP32 kernels.
+// (warp Cholesky, FP32) and the apply are those of the FP32 kernels.  The
+// residual update e_s -= <delta, f_s> is again a tensor-core product: the
+// staged tile times delta (split hi + lo, compensated the same way) as the
+// only non-zero column of an m16n8k16 B operand.
 #pragma once
 
 #include "k_sparse_impl.cuh"
@@ -54,24 +56,69 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// <v, hi + lo> over B coordinates of one staged row (16-byte shared loads).
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void *p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+// B fragments of delta (K = B coordinates, N = 8) with delta in column 0 and
+// zeros elsewhere, split delta = hi + lo.  Column 0 of an m16n8k16 B fragment
+// lives in lanes 0-3: register 0 holds k = 2 lane + {0, 1}, register 1 holds
+// k = 2 lane + 8 + {0, 1}.
 template <int B>
-__device__ __forceinline__ float dot_hilo(const float *v, const __nv_bfloat16 *h,
-                                          const __nv_bfloat16 *l) {
-    float t = 0.f;
+__device__ __forceinline__ void delta_frags(const float *v, int lane, unsigned (&dh)[B / 16][2],
+                                            unsigned (&dl)[B / 16][2]) {
 #pragma unroll
-    for (int j = 0; j < B; j += 8) {
-        const uint4 hv = *reinterpret_cast<const uint4 *>(h + j);
-        const uint4 lv = *reinterpret_cast<const uint4 *>(l + j);
-        const unsigned hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
+    for (int kb = 0; kb < B / 16; ++kb) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float2 fh = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hw[q]));
-            const float2 fl = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&lw[q]));
-            t += v[j + 2 * q] * (fh.x + fl.x) + v[j + 2 * q + 1] * (fh.y + fl.y);
+        for (int r = 0; r < 2; ++r) {
+            unsigned hw = 0u, lw = 0u;
+            if (lane < 4) {
+                const float2 x = *reinterpret_cast<const float2 *>(v + kb * 16 + 8 * r + 2 * lane);
+                const __nv_bfloat162 h = __floats2bfloat162_rn(x.x, x.y);
+                const float2 hf = __bfloat1622float2(h);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(x.x - hf.x, x.y - hf.y);
+                hw = *reinterpret_cast<const unsigned *>(&h);
+                lw = *reinterpret_cast<const unsigned *>(&l);
+            }
+            dh[kb][r] = hw;
+            dl[kb][r] = lw;
         }
     }
-    return t;
+}
+
+// Projections <delta, f_k> of the first 16 * nmt staged rows as the GEMV
+// [F_hi + F_lo] [delta_hi + delta_lo] on the tensor cores (compensated, lo*lo
+// dropped).  Row k's value is returned in lane k (k < 32; nmt <= 2).
+template <int B>
+__device__ __forceinline__ float project_mma(const __nv_bfloat16 *th, const __nv_bfloat16 *tl, int nmt,
+                                             const unsigned (&dh)[B / 16][2],
+                                             const unsigned (&dl)[B / 16][2], int lane) {
+    constexpr int SBH = BfCfg<B>::SBH;
+    const int q = lane >> 3, r8 = lane & 7;
+    float out = 0.f;
+#pragma unroll
+    for (int ms = 0; ms < 2; ++ms) {
+        if (ms >= nmt) break;
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kb = 0; kb < B / 16; ++kb) {
+            const int off = (ms * 16 + (q & 1) * 8 + r8) * SBH + kb * 16 + (q >> 1) * 8;
+            unsigned Fh[4], Fl[4];
+            ldsm_x4(Fh, th + off);
+            ldsm_x4(Fl, tl + off);
+            mma_bf16(d, Fh, dh[kb][0], dh[kb][1]);
+            mma_bf16(d, Fh, dl[kb][0], dl[kb][1]);
+            mma_bf16(d, Fl, dh[kb][0], dh[kb][1]);
+        }
+        // column 0: lane 4 g holds rows g (d[0]) and g + 8 (d[2])
+        const float v0 = __shfl_sync(kFull, d[0], 4 * r8);
+        const float v2 = __shfl_sync(kFull, d[2], 4 * r8);
+        if ((lane >> 4) == ms) out = (lane & 8) ? v2 : v0;
+    }
+    return out;
 }
 
 // Gather the hi and lo slices of `cnt` interactions (column id of interaction k in lane k).
@@ -262,9 +309,12 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
         __syncwarp();
         if (sub == 0) vv[col] = delta;
         __syncwarp();
+        unsigned dh[MT][2], dl[MT][2];
+        delta_frags<B>(vv, lane, dh, dl);
         if (nch == 1) {  // the slices are still in buffer 0
             const __nv_bfloat16 *th = th_of(0), *tl = th + C::TILE;
-            if (lane < tk.len) a.e[q0] -= dot_hilo<B>(vv, th + lane * SBH, tl + lane * SBH);
+            const float pr = project_mma<B>(th, tl, (tk.len + 15) >> 4, dh, dl, lane);
+            if (lane < tk.len) a.e[q0] -= pr;
             __syncwarp();
         } else if (nch > 1) {
             int64_t qc = 0;
@@ -295,7 +345,8 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
                 }
                 const int cnt = min(CH, tk.len - ch * CH);
                 const __nv_bfloat16 *th = th_of(bi), *tl = th + C::TILE;
-                if (lane < cnt) a.e[qc] -= dot_hilo<B>(vv, th + lane * SBH, tl + lane * SBH);
+                const float pr = project_mma<B>(th, tl, (cnt + 15) >> 4, dh, dl, lane);
+                if (lane < cnt) a.e[qc] -= pr;
                 __syncwarp();
                 qc = qn;
             }

@@ -33,7 +33,7 @@ struct SparseCfg {
     static constexpr int SB = B < 4 ? 4 : B + 4;   // shared row stride (floats)
     static constexpr int CH = 32;                  // interactions staged per chunk
     static constexpr int VPAD = (B + 3) / 4 * 4;
-    static constexpr int LSTR = B + 1;             // stride of the L factor copy
+    static constexpr int LSTR = B % 4 == 0 ? B + 4 : B + 1;  // stride of the L factor copy
     static constexpr int WARP_FLOATS_RAW = CH * SB + 3 * CH + VPAD + B * LSTR;
     static constexpr int WARP_FLOATS = (WARP_FLOATS_RAW + 3) / 4 * 4;
     static constexpr int GPP_FLOATS = (B * B + 3) / 4 * 4;
@@ -148,8 +148,19 @@ __device__ __forceinline__ bool chol_solve(float (&A)[B], float g, int col, int 
         float *v = cb + (k & 1) * B;
         if (sub == 0) v[col] = lck;
         __syncwarp();
+        if constexpr (B % 4 == 0) {  // 16-byte broadcasts of column k (v is 16-byte aligned)
 #pragma unroll
-        for (int j = k + 1; j < B; ++j) A[j] -= lck * v[j];
+            for (int j0 = (k + 1) & ~3; j0 < B; j0 += 4) {
+                const float4 q = *reinterpret_cast<const float4 *>(v + j0);
+                if (j0 > k) A[j0] -= lck * q.x;
+                if (j0 + 1 > k) A[j0 + 1] -= lck * q.y;
+                if (j0 + 2 > k) A[j0 + 2] -= lck * q.z;
+                A[j0 + 3] -= lck * q.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = k + 1; j < B; ++j) A[j] -= lck * v[j];
+        }
     }
     if (__any_sync(kFull, bad)) return false;
     // forward: L z = g
@@ -163,9 +174,16 @@ __device__ __forceinline__ bool chol_solve(float (&A)[B], float g, int col, int 
     // backward: L^T x = z, with the rows of L copied to shared memory
     __syncwarp();
     if (sub == 0) {
+        float *Lr = w.L + col * SparseCfg<B>::LSTR;
+        if constexpr (B % 4 == 0) {  // whole rows; entries right of the diagonal are never read
 #pragma unroll
-        for (int j = 0; j < B; ++j)
-            if (j <= col) w.L[col * SparseCfg<B>::LSTR + j] = A[j];
+            for (int j = 0; j < B; j += 4)
+                *reinterpret_cast<float4 *>(Lr + j) = make_float4(A[j], A[j + 1], A[j + 2], A[j + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < B; ++j)
+                if (j <= col) Lr[j] = A[j];
+        }
     }
     __syncwarp();
     float x = z;
@@ -607,7 +625,7 @@ __global__ void __launch_bounds__(256) k_split_solve(const StepArgs a) {
 
 template <int B>
 constexpr int split_solve_smem() {
-    return ((B * B + B + 3) / 4 * 4 + (B + 3) / 4 * 4 + B * (B + 1)) * 4;
+    return ((B * B + B + 3) / 4 * 4 + (B + 3) / 4 * 4 + B * SparseCfg<B>::LSTR) * 4;
 }
 
 // One warp per chunk of a split row: e_s -= <delta_row, f_{c_s,pi}>.
