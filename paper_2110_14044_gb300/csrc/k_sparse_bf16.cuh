@@ -14,7 +14,7 @@
 // applied) and are gathered with cp.async into two staging buffers.  One
 // ldmatrix.x4.trans of a 16 x 16 block serves both as the A fragment of an
 // m-tile and as the B fragments of the two matching n-tiles.  The Newton solve
-// (warp Cholesky, FP32) and the apply are those of the FP32 kernels.  The
+// (warp Gauss-Jordan, FP32) and the apply are those of the FP32 kernels.  The
 // residual update e_s -= <delta, f_s> is again a tensor-core product: the
 // staged tile times delta (split hi + lo, compensated the same way) as the
 // only non-zero column of an m16n8k16 B operand.
@@ -268,6 +268,12 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
                 for (int n = 0; n <= 2 * i + 1; ++n) {
                     *reinterpret_cast<float2 *>(As + (16 * i + r) * SA + 8 * n + c2) = make_float2(acc[t][0], acc[t][1]);
                     *reinterpret_cast<float2 *>(As + (16 * i + r + 8) * SA + 8 * n + c2) = make_float2(acc[t][2], acc[t][3]);
+                    if (n < 2 * i) {  // strictly below the diagonal blocks: mirror, the solver wants whole rows
+                        As[(8 * n + c2) * SA + 16 * i + r] = acc[t][0];
+                        As[(8 * n + c2 + 1) * SA + 16 * i + r] = acc[t][1];
+                        As[(8 * n + c2) * SA + 16 * i + r + 8] = acc[t][2];
+                        As[(8 * n + c2 + 1) * SA + 16 * i + r + 8] = acc[t][3];
+                    }
                     ++t;
                 }
                 if ((lane & 3) == 0) {

@@ -18,8 +18,8 @@
 //
 // Long rows are cut into several tasks that write partial (A, g) to a slot;
 // k_split_solve sums the slots of a row in slot order and solves it, and
-// k_split_resid applies its residual update.  A row whose FP32 Cholesky meets
-// a non-positive (or collapsed) pivot is queued; k_retry re-solves it in FP64
+// k_split_resid applies its residual update.  A row whose FP32 solve meets a
+// non-positive (or collapsed) pivot is queued; k_retry re-solves it in FP64
 // from scratch.
 #pragma once
 
@@ -33,8 +33,9 @@ struct SparseCfg {
     static constexpr int SB = B < 4 ? 4 : B + 4;   // shared row stride (floats)
     static constexpr int CH = 32;                  // interactions staged per chunk
     static constexpr int VPAD = (B + 3) / 4 * 4;
-    static constexpr int LSTR = B % 4 == 0 ? B + 4 : B + 1;  // stride of the L factor copy
-    static constexpr int WARP_FLOATS_RAW = CH * SB + 3 * CH + VPAD + B * LSTR;
+    static constexpr int CB = B % 4 == 0 ? B + 4 : B + 1;  // solver column buffer (B entries + g_k)
+    static constexpr int LREG = 2 * CB;                     // two column buffers
+    static constexpr int WARP_FLOATS_RAW = CH * SB + 3 * CH + VPAD + LREG;
     static constexpr int WARP_FLOATS = (WARP_FLOATS_RAW + 3) / 4 * 4;
     static constexpr int GPP_FLOATS = (B * B + 3) / 4 * 4;
     static constexpr int WARPS = 8;
@@ -46,8 +47,8 @@ struct WarpSmem {
     float *e;    // CH (alpha * e when weighted)
     float *a;    // CH alpha
     int *c;      // CH column ids
-    float *v;    // VPAD vector buffer (Cholesky column, delta)
-    float *L;    // B x (B+1) copy of the Cholesky factor
+    float *v;    // VPAD vector buffer (delta)
+    float *L;    // solver column buffers (2 x CB floats, 16-byte aligned)
 };
 
 template <int B>
@@ -118,83 +119,75 @@ __device__ __forceinline__ void stage_chunk(const StepArgs &a, int64_t begin, in
     __syncwarp();
 }
 
-// Warp Cholesky solve A delta = g.  Lane l holds row col = l % B of the
-// symmetric matrix in A[] (entries right of the diagonal may hold anything
-// finite) and entry col of g.  Right-looking factorisation, one column per
-// step: the pivot is broadcast with a shuffle and column k of L is exchanged
-// through a double-buffered column in w.L, so each step needs one __syncwarp.
-// Lane k checks its own pivot (positive, finite, and not below 1e-5 of its
-// original diagonal, i.e. no more than ~17 bits lost); one vote at the end
-// decides for the whole warp.  Returns false (warp-uniform) on a bad pivot or a
-// non-finite solution; on success `delta` holds entry col of the solution.
+// Approximate reciprocal (rcp.approx: at most 1 ulp from 1/x).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Newton solve A delta = g of one row in one warp: Gauss-Jordan elimination
+// without pivoting, which is sound for a symmetric positive definite A (its
+// pivots are the diagonal of D in A = L D L^T, i.e. the successive Schur
+// complements).  Lane l holds the whole row col = l % B of A (both triangles)
+// in A[] and entry col of g.  Step k: each lane publishes its column-k entry in
+// a double-buffered shared column (lane k also publishes g_k); every lane but
+// k then eliminates column k from its row and from g,
+//   s = A[col][k] / d_k,  A[col][j] -= s A[k][j] (j > k),  g_col -= s g_k,
+// where A[k][j] = A[j][k] is read from the published column (the trailing
+// block stays symmetric).  After B steps the system is diagonal and
+// delta_col = g_col / d_col.  Compared with Cholesky plus two substitutions
+// this has the same trailing-update work per lane (every lane runs every j
+// anyway) and a shorter dependent chain per step (store, warp barrier,
+// broadcast load, reciprocal), and no substitution passes.  Lane k checks its
+// own pivot (positive, finite, not below 1e-5 of its original diagonal, i.e.
+// no more than ~17 bits lost); one vote at the end decides for the warp.
+// Returns false (warp-uniform) on a bad pivot or a non-finite solution; on
+// success `delta` holds entry col of the solution.
 template <int B>
 __device__ __forceinline__ bool chol_solve(float (&A)[B], float g, int col, int sub,
                                            const WarpSmem &w, bool force_fail, float &delta) {
+    constexpr int CB = SparseCfg<B>::CB;  // column buffer: B entries, then g_k
     float diag0 = 0.f;
 #pragma unroll
     for (int j = 0; j < B; ++j)
         if (j == col) diag0 = A[j];
     bool bad = force_fail;
-    float inv_diag = 0.f;
-    float *cb = w.L;  // two column buffers of B floats while factorising
+    float dmine = 1.f;
+    float *cb = w.L;
 #pragma unroll
     for (int k = 0; k < B; ++k) {
-        if (col == k) bad = bad || !(A[k] > 1e-5f * diag0) || !(A[k] <= 3.0e38f);
-        const float akk = __shfl_sync(kFull, A[k], k);
-        const float inv = rsqrtf(fmaxf(akk, 1e-30f));
-        const float lck = A[k] * inv;
-        if (col == k) inv_diag = inv;
-        A[k] = lck;
-        float *v = cb + (k & 1) * B;
-        if (sub == 0) v[col] = lck;
+        float *v = cb + (k & 1) * CB;
+        if (sub == 0) {
+            v[col] = A[k];
+            if (col == k) v[B] = g;
+        }
         __syncwarp();
+        const float dk = v[k];
+        const float gk = v[B];
+        const float s = col == k ? 0.f : A[k] * rcp_approx(dk);
+        if (col == k) {
+            bad = bad || !(dk > 1e-5f * diag0) || !(dk <= 3.0e38f);
+            dmine = dk;
+        }
         if constexpr (B % 4 == 0) {  // 16-byte broadcasts of column k (v is 16-byte aligned)
 #pragma unroll
             for (int j0 = (k + 1) & ~3; j0 < B; j0 += 4) {
                 const float4 q = *reinterpret_cast<const float4 *>(v + j0);
-                if (j0 > k) A[j0] -= lck * q.x;
-                if (j0 + 1 > k) A[j0 + 1] -= lck * q.y;
-                if (j0 + 2 > k) A[j0 + 2] -= lck * q.z;
-                A[j0 + 3] -= lck * q.w;
+                if (j0 > k) A[j0] -= s * q.x;
+                if (j0 + 1 > k) A[j0 + 1] -= s * q.y;
+                if (j0 + 2 > k) A[j0 + 2] -= s * q.z;
+                A[j0 + 3] -= s * q.w;
             }
         } else {
 #pragma unroll
-            for (int j = k + 1; j < B; ++j) A[j] -= lck * v[j];
+            for (int j = k + 1; j < B; ++j) A[j] -= s * v[j];
         }
+        g -= s * gk;
     }
     if (__any_sync(kFull, bad)) return false;
-    // forward: L z = g
-    float z = g;
-#pragma unroll
-    for (int k = 0; k < B; ++k) {
-        const float zk = __shfl_sync(kFull, z * inv_diag, k);
-        if (col > k) z -= A[k] * zk;
-        else if (col == k) z = zk;
-    }
-    // backward: L^T x = z, with the rows of L copied to shared memory
-    __syncwarp();
-    if (sub == 0) {
-        float *Lr = w.L + col * SparseCfg<B>::LSTR;
-        if constexpr (B % 4 == 0) {  // whole rows; entries right of the diagonal are never read
-#pragma unroll
-            for (int j = 0; j < B; j += 4)
-                *reinterpret_cast<float4 *>(Lr + j) = make_float4(A[j], A[j + 1], A[j + 2], A[j + 3]);
-        } else {
-#pragma unroll
-            for (int j = 0; j < B; ++j)
-                if (j <= col) Lr[j] = A[j];
-        }
-    }
-    __syncwarp();
-    float x = z;
-#pragma unroll
-    for (int k = B - 1; k >= 0; --k) {
-        const float xk = __shfl_sync(kFull, x * inv_diag, k);
-        if (col < k) x -= w.L[k * SparseCfg<B>::LSTR + col] * xk;
-        else if (col == k) x = xk;
-    }
-    delta = x;
-    return __all_sync(kFull, isfinite(x));
+    delta = g / dmine;
+    return __all_sync(kFull, isfinite(delta));
 }
 
 template <int B>
@@ -317,7 +310,7 @@ __global__ void __launch_bounds__(256, 2) k_sparse(const StepArgs a) {
 // grp + 3, ...) and owns tile t = l % 10, so every staged interaction costs a
 // lane T*T FMAs with 2 T / 4 shared loads.  The three group partials are summed
 // in a fixed order into a shared copy of A_r, whose rows then feed the same
-// warp Cholesky as k_sparse.  Slices are gathered with cp.async into two
+// warp solver as k_sparse.  Slices are gathered with cp.async into two
 // staging buffers, so the next 32 interactions load while the current ones are
 // multiplied.
 template <int B>
@@ -407,12 +400,11 @@ __global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
     float *const she = wbase + 2 * C::BUF;
     float *const sha = she + 2 * CH;
     float *gs = wbase + 2 * C::BUF + 4 * CH;   // gradient (B)
-    float *vv = gs + C::VEC;                   // delta / Cholesky column (B)
-    for (int i = lane; i < C::BUF; i += 32) wbase[C::BUF + i] = 0.f;  // finite values above the diagonal
+    float *vv = gs + C::VEC;                   // delta (B)
     __syncthreads();
     WarpSmem w;
     w.v = vv;
-    w.L = wbase + C::BUF;  // the factor copy reuses the second staging buffer
+    w.L = wbase + C::BUF;  // the solver's column buffers reuse the second staging buffer
     const int col = lane % B, sub = lane / B;
     const bool active = lane < C::ACTIVE;
     const int grp = active ? lane / C::NT : C::NG, t = lane % C::NT;
@@ -505,11 +497,18 @@ __global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
             }
             __syncwarp();
         }
+        // row col of A_r, both triangles: only tiles on or below the diagonal
+        // were formed, so entries right of the diagonal come from column col
         float A[B];
 #pragma unroll
         for (int j = 0; j < B; j += 4) {
             const float4 v = *reinterpret_cast<const float4 *>(As + col * SB + j);
             A[j] = v.x; A[j + 1] = v.y; A[j + 2] = v.z; A[j + 3] = v.w;
+        }
+#pragma unroll
+        for (int j = 1; j < B; ++j) {
+            const float u = As[j * SB + col];
+            if (j > col) A[j] = u;
         }
         float g = gs[col];
         __syncwarp();
@@ -625,7 +624,7 @@ __global__ void __launch_bounds__(256) k_split_solve(const StepArgs a) {
 
 template <int B>
 constexpr int split_solve_smem() {
-    return ((B * B + B + 3) / 4 * 4 + (B + 3) / 4 * 4 + B * SparseCfg<B>::LSTR) * 4;
+    return ((B * B + B + 3) / 4 * 4 + (B + 3) / 4 * 4 + SparseCfg<B>::LREG) * 4;
 }
 
 // One warp per chunk of a split row: e_s -= <delta_row, f_{c_s,pi}>.
