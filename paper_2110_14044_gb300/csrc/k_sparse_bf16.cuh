@@ -151,8 +151,9 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
     char *sm = reinterpret_cast<char *>(smem4);
     float *sGpp = reinterpret_cast<float *>(sm);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // alpha0 G_pipi, exactly symmetric, read by columns (as in the FP32 kernels)
     for (int i = threadIdx.x; i < B * B; i += blockDim.x)
-        sGpp[i] = a.alpha0 * a.G[(int64_t)(a.p0 + i / B) * B + (i % B)];
+        sGpp[i] = a.alpha0 * a.G[(int64_t)(a.p0 + max(i / B, i % B)) * B + min(i / B, i % B)];
     char *wb = sm + B * B * 4 + warp * C::WARP_BYTES;
     // staging buffer bi: hi tile at wb + bi * BUF_BYTES, lo tile right after it
     auto th_of = [&](int bi) { return reinterpret_cast<__nv_bfloat16 *>(wb + bi * C::BUF_BYTES); };
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
         const int row = tk.row;
         const float lam = a.lambda * (1.0f + a.nu * (float)tk.len);
 #pragma unroll
-        for (int j = 0; j < B; ++j) A[j] += sGpp[col * B + j] + (j == col ? lam : 0.f);
+        for (int j = 0; j < B; ++j) A[j] += sGpp[j * B + col] + (j == col ? lam : 0.f);
         g += a.R[(int64_t)row * B + col];
         float delta;
         if (!chol_solve<B>(A, g, col, sub, w, a.force_fp64 != 0, delta)) {

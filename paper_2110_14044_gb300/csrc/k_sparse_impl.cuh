@@ -222,8 +222,11 @@ __global__ void __launch_bounds__(256, 2) k_sparse(const StepArgs a) {
     float *smem = reinterpret_cast<float *>(smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *sGpp = smem;
+    // alpha0 G_pipi, exactly symmetric (taken from its lower triangle: the solver
+    // treats the trailing block as symmetric); lane col reads column col, which
+    // is free of bank conflicts
     for (int i = threadIdx.x; i < B * B; i += blockDim.x)
-        sGpp[i] = a.alpha0 * a.G[(int64_t)(a.p0 + i / B) * B + (i % B)];
+        sGpp[i] = a.alpha0 * a.G[(int64_t)(a.p0 + max(i / B, i % B)) * B + min(i / B, i % B)];
     __syncthreads();
     const WarpSmem w = warp_smem<B>(smem, warp);
     const int col = lane % B, sub = lane / B;
@@ -392,8 +395,11 @@ __global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
     float *smem = reinterpret_cast<float *>(smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *sGpp = smem;
+    // alpha0 G_pipi, exactly symmetric (taken from its lower triangle: the solver
+    // treats the trailing block as symmetric); lane col reads column col, which
+    // is free of bank conflicts
     for (int i = threadIdx.x; i < B * B; i += blockDim.x)
-        sGpp[i] = a.alpha0 * a.G[(int64_t)(a.p0 + i / B) * B + (i % B)];
+        sGpp[i] = a.alpha0 * a.G[(int64_t)(a.p0 + max(i / B, i % B)) * B + min(i / B, i % B)];
     float *wbase = smem + B * B + warp * C::WARP_FLOATS;
     // buffer bi (0 or 1): slices at wbase + bi * BUF, residuals at she + bi * CH,
     // weights at sha + bi * CH
@@ -525,7 +531,7 @@ __global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
         const int row = tk.row;
         const float lam = a.lambda * (1.0f + a.nu * (float)tk.len);
 #pragma unroll
-        for (int j = 0; j < B; ++j) A[j] += sGpp[col * B + j] + (j == col ? lam : 0.f);
+        for (int j = 0; j < B; ++j) A[j] += sGpp[j * B + col] + (j == col ? lam : 0.f);
         g += a.R[(int64_t)row * B + col];
         float delta;
         if (!chol_solve<B>(A, g, col, sub, w, a.force_fp64 != 0, delta)) {
@@ -606,7 +612,7 @@ __global__ void __launch_bounds__(256) k_split_solve(const StepArgs a) {
             const float lam = a.lambda * (1.0f + a.nu * (float)sr.len);
 #pragma unroll
             for (int j = 0; j < B; ++j)
-                acc[j] += a.alpha0 * a.G[(int64_t)(a.p0 + j) * B + col] + (j == col ? lam : 0.f);
+                acc[j] += a.alpha0 * a.G[(int64_t)(a.p0 + max(j, col)) * B + min(j, col)] + (j == col ? lam : 0.f);
             g += a.R[(int64_t)sr.row * B + col];
             float delta = 0.f;
             const bool ok = chol_solve<B>(acc, g, col, sub, w, a.force_fp64 != 0, delta);
@@ -742,7 +748,7 @@ __global__ void __launch_bounds__(128) k_retry(const StepArgs a) {
         const double lam = (double)a.lambda * (1.0 + (double)a.nu * (double)(end - beg));
 #pragma unroll
         for (int j = 0; j < B; ++j)
-            A[j] += (double)a.alpha0 * (double)a.G[(int64_t)(a.p0 + j) * B + col] +
+            A[j] += (double)a.alpha0 * (double)a.G[(int64_t)(a.p0 + max(j, col)) * B + min(j, col)] +
                     (j == col ? lam : 0.0);
         g += (double)a.R[(int64_t)row * B + col];
         // right-looking Cholesky, lane col holds row col
