@@ -224,6 +224,12 @@ ials_status upload(ials_ctx *c, const void *src, void *dst, size_t bytes, const 
     return IALS_OK;
 }
 
+// Residual cache e = W H^T - y (Alg. 3 "Compute yhat") over the user-side tasks.
+cudaError_t residual_enqueue(ials_ctx *c) {
+    return launch_residual_tasks(c->side[0].tasks, c->side[0].n_tasks, c->side[0].idx, c->W, c->H, c->y,
+                                 c->p.d, c->e, c->ctl, c->stream);
+}
+
 ials_status step_enqueue(ials_ctx *c, int side, int block, Profiler *prof = nullptr) {
     const int32_t d = c->p.d, b = c->p.b, p0 = block * b;
     SideDev &sd = c->side[side];
@@ -295,9 +301,7 @@ ials_status step_enqueue(ials_ctx *c, int side, int block, Profiler *prof = null
 
 ials_status epoch_enqueue(ials_ctx *c, Profiler *prof = nullptr) {
     prof_mark(prof, K_RESIDUAL, c->stream);
-    IALS_CUDA(launch_residual(c->side[0].ptr, c->side[0].idx, c->W, c->H, c->y, c->n_users,
-                              c->p.d, c->e, c->stream),
-              "residual recompute");
+    IALS_CUDA(residual_enqueue(c), "residual recompute");
     prof_mark(prof, -1, c->stream);
     const int nb = c->p.d / c->p.b;
     for (int k = 0; k < nb; ++k)
@@ -553,8 +557,7 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
         return fail(IALS_ECUDA, "could not encode TMA tensor maps (cuTensorMapEncodeTiled)");
     }
     cudaError_t e4 = cudaStreamSynchronize(c->stream);
-    cudaError_t e5 = launch_residual(c->side[0].ptr, c->side[0].idx, c->W, c->H, c->y, n_users, d,
-                                     c->e, c->stream);
+    cudaError_t e5 = residual_enqueue(c);
     cudaError_t e6 = cudaStreamSynchronize(c->stream);
     // Set kernel attributes of both sides' sparse variants now, outside any
     // stream capture: an empty step launches nothing but the (idle) retry kernel.
@@ -659,18 +662,14 @@ ials_status ials_set_factors(ials_ctx *c, const float *W, const float *H) {
     if (H && c->Hh)
         IALS_CUDA(launch_split_bf16(c->H, (int64_t)c->n_items * c->p.d, c->Hh, c->Hl, c->stream), "H shadow");
     // the residual cache is a function of W and H: keep it consistent
-    IALS_CUDA(launch_residual(c->side[0].ptr, c->side[0].idx, c->W, c->H, c->y, c->n_users,
-                              c->p.d, c->e, c->stream),
-              "residual recompute");
+    IALS_CUDA(residual_enqueue(c), "residual recompute");
     IALS_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
     return IALS_OK;
 }
 
 ials_status ials_recompute_residuals(ials_ctx *c) {
     if (!c) return fail(IALS_EINVAL, "bad context");
-    IALS_CUDA(launch_residual(c->side[0].ptr, c->side[0].idx, c->W, c->H, c->y, c->n_users,
-                              c->p.d, c->e, c->stream),
-              "residual recompute");
+    IALS_CUDA(residual_enqueue(c), "residual recompute");
     IALS_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
     return IALS_OK;
 }

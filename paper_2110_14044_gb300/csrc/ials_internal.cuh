@@ -130,6 +130,11 @@ struct FoldArgs {
 cudaError_t launch_residual(const int64_t *u_ptr, const int32_t *u_idx, const float *W,
                             const float *H, const float *y, int32_t n_users, int32_t d,
                             float *e, cudaStream_t s);
+// e = W H^T - y over the user-side task list (persistent, work-stealing over an
+// atomic counter, which the launcher zeroes on the stream first).
+cudaError_t launch_residual_tasks(const Task *tasks, int32_t n_tasks, const int32_t *u_idx,
+                                  const float *W, const float *H, const float *y, int32_t d, float *e,
+                                  int32_t *counter, cudaStream_t s);
 // Sum over S of alpha (yhat - y)^2 in FP64, recomputing yhat from W, H.
 // Writes one double per block into part (n_part >= grid) and the total into out.
 cudaError_t launch_sq_loss(const int64_t *u_ptr, const int32_t *u_idx, const float *W,

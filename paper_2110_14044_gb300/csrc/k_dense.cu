@@ -108,6 +108,85 @@ __global__ void __launch_bounds__(256) k_residual(const int64_t *__restrict__ u_
     }
 }
 
+// Residual cache e = W H^T - y over S (Alg. 3, "Compute yhat"), persistent and
+// work-stealing: warps take the user-side tasks (rows, or pieces of long rows;
+// the list is sorted by decreasing length) from an atomic counter, so the long
+// rows start first and no warp idles while work remains.  Lane layout as in
+// k_residual (sub-groups of SG lanes per interaction, U interactions in flight
+// per sub-group); the column ids of the next 32 interactions are loaded before
+// the current 32 are processed.  Each e_s is written once by one lane, so the
+// result does not depend on the schedule.
+template <int SGL, int MAXV>
+__global__ void __launch_bounds__(256) k_residual_tasks(const Task *__restrict__ tasks, int32_t n_tasks,
+                                                        const int32_t *__restrict__ u_idx,
+                                                        const float *__restrict__ W,
+                                                        const float *__restrict__ H,
+                                                        const float *__restrict__ y, int32_t d,
+                                                        float *__restrict__ e, int32_t *counter) {
+    constexpr int SG = 1 << SGL, NSUB = 32 / SG;
+    constexpr int UMAX = MAXV >= 16 ? 1 : (MAXV >= 8 ? 2 : 4);
+    constexpr int U = SG < UMAX ? SG : UMAX;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane >> SGL, sl = lane & (SG - 1);
+    const int nv4 = d >> 2;
+    const float4 *W4 = reinterpret_cast<const float4 *>(W);
+    const float4 *H4 = reinterpret_cast<const float4 *>(H);
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= n_tasks) break;
+        const Task tk = tasks[t];
+        const int64_t beg = tk.begin, end = tk.begin + tk.len;
+        float4 wv[MAXV];
+#pragma unroll
+        for (int m = 0; m < MAXV; ++m) {
+            const int v = sl + m * SG;
+            wv[m] = v < nv4 ? W4[(int64_t)tk.row * nv4 + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        int my_c = beg + lane < end ? u_idx[beg + lane] : 0;
+        for (int64_t s0 = beg; s0 < end; s0 += 32) {
+            const int cnt = (int)min((int64_t)32, end - s0);
+            const int nxt_c = s0 + 32 + lane < end ? u_idx[s0 + 32 + lane] : 0;
+#pragma unroll
+            for (int m0 = 0; m0 < SG; m0 += U) {
+                float acc[U];
+                float4 h[U][MAXV];
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    const int k = sub + NSUB * (m0 + q);
+                    const int64_t c = __shfl_sync(kFull, my_c, k);
+                    acc[q] = 0.f;
+#pragma unroll
+                    for (int m = 0; m < MAXV; ++m) {
+                        const int v = sl + m * SG;
+                        h[q][m] = (k < cnt && v < nv4) ? __ldg(H4 + c * nv4 + v)
+                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+#pragma unroll
+                    for (int m = 0; m < MAXV; ++m) acc[q] += dot4(wv[m], h[q][m]);
+#pragma unroll
+                    for (int o = SG >> 1; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(kFull, acc[q], o);
+                }
+                if (sl == 0) {
+#pragma unroll
+                    for (int q = 0; q < U; ++q) {
+                        const int k = sub + NSUB * (m0 + q);
+                        if (k < cnt) {
+                            const int64_t s = s0 + k;
+                            e[s] = acc[q] - (y ? y[s] : 1.0f);
+                        }
+                    }
+                }
+            }
+            my_c = nxt_c;
+        }
+    }
+}
+
 // Fixed-order sum of n doubles by one block; *out = (acc ? *out : 0) + scale * sum.
 __global__ void k_sum_parts(const double *__restrict__ part, int32_t n, double scale,
                             double *out, int acc) {
@@ -405,6 +484,24 @@ cudaError_t launch_residual_impl(const int64_t *u_ptr, const int32_t *u_idx, con
     return cudaGetLastError();
 }
 
+template <int SGL, int MV>
+cudaError_t launch_residual_tasks_t(const Task *tasks, int32_t n_tasks, const int32_t *u_idx,
+                                    const float *W, const float *H, const float *y, int32_t d,
+                                    float *e, int32_t *counter, cudaStream_t s) {
+    static int per_sm = 0;  // resident blocks per SM (same for every context)
+    if (per_sm == 0) {
+        int n = 0;
+        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_residual_tasks<SGL, MV>, 256, 0);
+        if (err != cudaSuccess) return err;
+        per_sm = n > 0 ? n : 1;
+    }
+    int grid = per_sm * kSMs;
+    const int need = (n_tasks + 7) / 8;
+    if (grid > need) grid = need > 0 ? need : 1;
+    k_residual_tasks<SGL, MV><<<grid, 256, 0, s>>>(tasks, n_tasks, u_idx, W, H, y, d, e, counter);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_residual(const int64_t *u_ptr, const int32_t *u_idx, const float *W,
@@ -413,6 +510,36 @@ cudaError_t launch_residual(const int64_t *u_ptr, const int32_t *u_idx, const fl
     if (n_users == 0) return cudaSuccess;
     return launch_residual_impl<false>(u_ptr, u_idx, W, H, y, nullptr, n_users, d, e, nullptr,
                                        residual_grid(n_users), s);
+}
+
+cudaError_t launch_residual_tasks(const Task *tasks, int32_t n_tasks, const int32_t *u_idx,
+                                  const float *W, const float *H, const float *y, int32_t d, float *e,
+                                  int32_t *counter, cudaStream_t s) {
+    if (n_tasks == 0) return cudaSuccess;
+    cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
+    if (err != cudaSuccess) return err;
+    // same sub-group choice as launch_residual_impl
+    const int nv4 = d / 4;
+    int sg_log = 0;
+    while ((2 << sg_log) <= 32 && (2 << sg_log) * 4 <= nv4) ++sg_log;
+    const int SG = 1 << sg_log;
+    const int maxv = (nv4 + SG - 1) / SG;
+#define IALS_REST(SGL, MV) return launch_residual_tasks_t<SGL, MV>(tasks, n_tasks, u_idx, W, H, y, d, e, counter, s)
+    if (sg_log == 0) {
+        if (maxv <= 1) IALS_REST(0, 1);
+        else if (maxv <= 2) IALS_REST(0, 2);
+        else if (maxv <= 4) IALS_REST(0, 4);
+        else IALS_REST(0, 8);
+    } else if (sg_log == 1) { if (maxv <= 4) IALS_REST(1, 4); else IALS_REST(1, 8); }
+    else if (sg_log == 2) { if (maxv <= 4) IALS_REST(2, 4); else IALS_REST(2, 8); }
+    else if (sg_log == 3) { if (maxv <= 4) IALS_REST(3, 4); else IALS_REST(3, 8); }
+    else if (sg_log == 4) { if (maxv <= 4) IALS_REST(4, 4); else IALS_REST(4, 8); }
+    else if (maxv <= 4) IALS_REST(5, 4);
+    else if (maxv <= 8) IALS_REST(5, 8);
+    else if (maxv <= 16) IALS_REST(5, 16);
+    else if (maxv <= 32) IALS_REST(5, 32);
+#undef IALS_REST
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_sq_loss(const int64_t *u_ptr, const int32_t *u_idx, const float *W,
