@@ -365,7 +365,6 @@ template <int B, bool PERM>
 cudaError_t launch_sparse_bf16_all(const StepArgs &a, cudaStream_t s) {
     using C = BfCfg<B>;
     using T = TileCfg<B>;
-    constexpr int RS = 8 * (2 * T::BUF + T::VEC) * 4;
     static bool attr_done = false;
     static int per_sm = 0;
     if (!attr_done) {
@@ -374,8 +373,6 @@ cudaError_t launch_sparse_bf16_all(const StepArgs &a, cudaStream_t s) {
                                       C::SMEM_BYTES)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(k_split_solve<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       split_solve_smem<B>())) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_split_resid_tiled<B, PERM>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, RS)) != cudaSuccess) return e;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sparse_bf16<B, PERM>,
                                                                C::WARPS * 32, C::SMEM_BYTES)) != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
@@ -395,12 +392,9 @@ cudaError_t launch_sparse_bf16_all(const StepArgs &a, cudaStream_t s) {
         k_split_solve<B><<<g2, 256, split_solve_smem<B>(), s>>>(a);
         prof_mark(a.prof, -1, s);
     }
-    if (a.n_stasks > 0) {
-        int g3 = (a.n_stasks + 7) / 8;
-        if (g3 > 152 * 8) g3 = 152 * 8;
-        prof_mark(a.prof, K_SPLIT_RESID, s);
-        k_split_resid_tiled<B, PERM><<<g3, 256, RS, s>>>(a);
-        prof_mark(a.prof, -1, s);
+    {  // always called: the first call sizes the grid, outside any stream capture
+        const cudaError_t e = launch_split_resid_reg<B, PERM>(a, s);
+        if (e != cudaSuccess) return e;
     }
     prof_mark(a.prof, K_RETRY, s);
     k_retry<B, PERM, false><<<38, 128, 0, s>>>(a);

@@ -488,7 +488,6 @@ cudaError_t launch_sparse_cta_all(const StepArgs &a, cudaStream_t s) {
     using C = CtaCfg<B>;
     static bool attr_done = false;
     static int per_sm = 0;
-    constexpr int RS = 8 * (2 * TileCfg<B>::BUF + TileCfg<B>::VEC) * 4 * 32 / B;  // warps scale 1/B
     if (!attr_done) {
         cudaError_t e;
         if ((e = cudaFuncSetAttribute(k_sparse_cta<B, PERM, HAS_A>,
@@ -497,8 +496,6 @@ cudaError_t launch_sparse_cta_all(const StepArgs &a, cudaStream_t s) {
                                       C::SMEM_BYTES)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(k_retry_cta<B, PERM, HAS_A>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, retry_cta_smem<B>())) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_split_resid_tiled<B, PERM>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, RS)) != cudaSuccess) return e;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sparse_cta<B, PERM, HAS_A>,
                                                                C::THREADS, C::SMEM_BYTES)) != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
@@ -517,13 +514,9 @@ cudaError_t launch_sparse_cta_all(const StepArgs &a, cudaStream_t s) {
         k_split_solve_cta<B><<<g2, C::THREADS, C::SMEM_BYTES, s>>>(a);
         prof_mark(a.prof, -1, s);
     }
-    if (a.n_stasks > 0) {
-        constexpr int WARPS = 8 * 32 / B;
-        int g3 = (a.n_stasks + WARPS - 1) / WARPS;
-        if (g3 > 152 * 8) g3 = 152 * 8;
-        prof_mark(a.prof, K_SPLIT_RESID, s);
-        k_split_resid_tiled<B, PERM><<<g3, WARPS * 32, RS, s>>>(a);
-        prof_mark(a.prof, -1, s);
+    {  // always called: the first call sizes the grid, outside any stream capture
+        const cudaError_t e = launch_split_resid_reg<B, PERM>(a, s);
+        if (e != cudaSuccess) return e;
     }
     prof_mark(a.prof, K_RETRY, s);
     k_retry_cta<B, PERM, HAS_A><<<76, C::THREADS, retry_cta_smem<B>(), s>>>(a);

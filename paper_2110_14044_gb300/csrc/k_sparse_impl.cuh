@@ -656,57 +656,120 @@ __global__ void __launch_bounds__(256) k_split_resid(const StepArgs a, const Tas
     }
 }
 
-// One warp per piece (<= 128 interactions) of a split row: e_s -= <delta_row,
-// f_{c_s,pi}>, with the slices gathered by cp.async into two staging buffers
-// and the column ids / residual positions loaded one chunk ahead.
+// Residual update of split rows with register gathers (B a multiple of 4):
+// e_s -= <delta_row, f_{c_s,pi}> over the pieces (<= 128 interactions) of the
+// split rows.  Persistent: warps take pieces from an atomic counter (zeroed by
+// the launcher; the list is sorted by decreasing length).  SG lanes share an
+// interaction (MAXV float4 each), U interactions per sub-group are loaded
+// before any is reduced, and the column ids and residual positions of the
+// next 32 interactions are loaded before the current ones are used.  Pieces
+// are disjoint and each e_s is updated by one lane, so the result does not
+// depend on the schedule.
+template <int B>
+struct ResRegCfg {
+    static constexpr int NV4 = B / 4;
+    static constexpr int sgl() {
+        int g = 0;
+        while ((2 << g) <= 32 && (2 << g) * 4 <= NV4) ++g;
+        return g;
+    }
+    static constexpr int SGL = sgl(), SG = 1 << SGL, NSUB = 32 / SG;
+    static constexpr int MAXV = (NV4 + SG - 1) / SG;
+    static constexpr int UMAX = MAXV >= 16 ? 1 : (MAXV >= 8 ? 2 : 4);
+    static constexpr int U = SG < UMAX ? SG : UMAX;
+};
+
 template <int B, bool PERM>
-__global__ void __launch_bounds__(256) k_split_resid_tiled(const StepArgs a) {
-    using C = TileCfg<B>;
-    constexpr int SB = C::SB, CH = C::CH;
-    extern __shared__ float4 smem4[];
-    float *smem = reinterpret_cast<float *>(smem4);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *wbase = smem + warp * (2 * C::BUF + C::VEC);
-    float *vv = wbase + 2 * C::BUF;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.n_stasks; t += nw) {
+__global__ void __launch_bounds__(256) k_split_resid_reg(const StepArgs a) {
+    using C = ResRegCfg<B>;
+    constexpr int SGL = C::SGL, SG = C::SG, NSUB = C::NSUB, MAXV = C::MAXV, U = C::U, NV4 = C::NV4;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane >> SGL, sl = lane & (SG - 1);
+    const float4 *F4 = reinterpret_cast<const float4 *>(a.F);
+    const float4 *D4 = reinterpret_cast<const float4 *>(a.delta);
+    const int64_t d4 = a.d >> 2, p4 = a.p0 >> 2;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(a.counter, 1);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= a.n_stasks) break;
         const Task tk = a.stasks[t];
-        __syncwarp();
-        for (int j = lane; j < B; j += 32) vv[j] = a.delta[(int64_t)tk.srow * B + j];
-        const int nch = (tk.len + CH - 1) / CH;
-        int cB = 0;
-        int64_t qB = 0;
-        auto meta = [&](int j) {
-            const int cnt = min(CH, tk.len - j * CH);
-            if (lane < cnt) {
-                const int64_t s = tk.begin + (int64_t)j * CH + lane;
-                cB = a.idx[s];
-                qB = PERM ? (int64_t)a.pos[s] : s;
+        float4 dv[MAXV];
+#pragma unroll
+        for (int m = 0; m < MAXV; ++m) {
+            const int v = sl + m * SG;
+            dv[m] = v < NV4 ? D4[(int64_t)tk.srow * NV4 + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const int64_t beg = tk.begin, end = tk.begin + tk.len;
+        int my_c = 0, my_q = 0;
+        if (beg + lane < end) {
+            my_c = a.idx[beg + lane];
+            my_q = PERM ? a.pos[beg + lane] : (int)(beg + lane);
+        }
+        for (int64_t s0 = beg; s0 < end; s0 += 32) {
+            const int cnt = (int)min((int64_t)32, end - s0);
+            int nx_c = 0, nx_q = 0;
+            if (s0 + 32 + lane < end) {
+                nx_c = a.idx[s0 + 32 + lane];
+                nx_q = PERM ? a.pos[s0 + 32 + lane] : (int)(s0 + 32 + lane);
             }
-        };
-        meta(0);
-        int64_t qc = qB;
-        gather_async<B>(wbase, a.F, a.d, a.p0, cB, min(CH, tk.len), lane);
-        cp_async_commit();
-        if (nch > 1) meta(1);
-        for (int ch = 0; ch < nch; ++ch) {
-            const int bi = ch & 1;
-            cp_async_wait_all();
-            __syncwarp();
-            int64_t qn = 0;
-            if (ch + 1 < nch) {
-                gather_async<B>(wbase + (bi ^ 1) * C::BUF, a.F, a.d, a.p0, cB,
-                                min(CH, tk.len - (ch + 1) * CH), lane);
-                cp_async_commit();
-                qn = qB;
-                if (ch + 2 < nch) meta(ch + 2);
+#pragma unroll
+            for (int m0 = 0; m0 < SG; m0 += U) {
+                float acc[U];
+                float4 h[U][MAXV];
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    const int k = sub + NSUB * (m0 + q);
+                    const int64_t c = __shfl_sync(kFull, my_c, k);
+                    acc[q] = 0.f;
+#pragma unroll
+                    for (int m = 0; m < MAXV; ++m) {
+                        const int v = sl + m * SG;
+                        h[q][m] = (k < cnt && v < NV4) ? __ldg(F4 + c * d4 + p4 + v)
+                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+#pragma unroll
+                    for (int m = 0; m < MAXV; ++m)
+                        acc[q] += dv[m].x * h[q][m].x + dv[m].y * h[q][m].y + dv[m].z * h[q][m].z +
+                                  dv[m].w * h[q][m].w;
+#pragma unroll
+                    for (int o = SG >> 1; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(kFull, acc[q], o);
+                }
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    const int k = sub + NSUB * (m0 + q);
+                    const int qk = __shfl_sync(kFull, my_q, k);
+                    if (sl == 0 && k < cnt) a.e[qk] -= acc[q];
+                }
             }
-            const int cnt = min(CH, tk.len - ch * CH);
-            if (lane < cnt) a.e[qc] -= dot_slice<B>(vv, wbase + bi * C::BUF + lane * SB);
-            __syncwarp();
-            qc = qn;
+            my_c = nx_c;
+            my_q = nx_q;
         }
     }
+}
+
+template <int B, bool PERM>
+cudaError_t launch_split_resid_reg(const StepArgs &a, cudaStream_t s) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int n = 0;
+        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_split_resid_reg<B, PERM>, 256, 0);
+        if (err != cudaSuccess) return err;
+        per_sm = n > 0 ? n : 1;
+    }
+    if (a.n_stasks <= 0) return cudaSuccess;
+    cudaError_t err = cudaMemsetAsync(a.counter, 0, sizeof(int32_t), s);
+    if (err != cudaSuccess) return err;
+    int grid = 152 * per_sm;
+    const int need = (a.n_stasks + 7) / 8;
+    if (grid > need) grid = need;
+    prof_mark(a.prof, K_SPLIT_RESID, s);
+    k_split_resid_reg<B, PERM><<<grid, 256, 0, s>>>(a);
+    prof_mark(a.prof, -1, s);
+    return cudaGetLastError();
 }
 
 // FP64 re-solve of queued rows: statistics accumulated from scratch in FP64
@@ -833,15 +896,10 @@ cudaError_t launch_step_b(const StepArgs &a, cudaStream_t s) {
         cudaError_t e1 = cudaFuncSetAttribute(kmain, cudaFuncAttributeMaxDynamicSharedMemorySize, MAIN_SMEM);
         cudaError_t e2 = cudaFuncSetAttribute(k_split_solve<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               split_solve_smem<B>());
-        cudaError_t e3;
-        if constexpr (B >= 8) {
-            constexpr int RS = 8 * (2 * TileCfg<(B >= 8 ? B : 8)>::BUF + TileCfg<(B >= 8 ? B : 8)>::VEC) * 4;
-            e3 = cudaFuncSetAttribute(k_split_resid_tiled<B, PERM>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, RS);
-        } else {
+        cudaError_t e3 = cudaSuccess;
+        if constexpr (B % 4 != 0)
             e3 = cudaFuncSetAttribute(k_split_resid<B, PERM>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
-        }
         if (e1 != cudaSuccess) return e1;
         if (e2 != cudaSuccess) return e2;
         if (e3 != cudaSuccess) return e3;
@@ -871,16 +929,14 @@ cudaError_t launch_step_b(const StepArgs &a, cudaStream_t s) {
 template <int B, bool PERM, bool HAS_A>
 cudaError_t launch_split_resid_b(const StepArgs &a, cudaStream_t s) {
     using C = SparseCfg<B>;
-    if (a.n_stasks > 0) {
+    if constexpr (B % 4 == 0) {
+        cudaError_t e = launch_split_resid_reg<B, PERM>(a, s);
+        if (e != cudaSuccess) return e;
+    } else if (a.n_stasks > 0) {
         int g3 = (a.n_stasks + C::WARPS - 1) / C::WARPS;
         if (g3 > 152 * 8) g3 = 152 * 8;
         prof_mark(a.prof, K_SPLIT_RESID, s);
-        if constexpr (B >= 8) {
-            constexpr int RS = 8 * (2 * TileCfg<(B >= 8 ? B : 8)>::BUF + TileCfg<(B >= 8 ? B : 8)>::VEC) * 4;
-            k_split_resid_tiled<B, PERM><<<g3, 256, RS, s>>>(a);
-        } else {
-            k_split_resid<B, PERM><<<g3, C::WARPS * 32, C::SMEM_BYTES, s>>>(a, a.stasks, a.n_stasks);
-        }
+        k_split_resid<B, PERM><<<g3, C::WARPS * 32, C::SMEM_BYTES, s>>>(a, a.stasks, a.n_stasks);
         prof_mark(a.prof, -1, s);
     }
     prof_mark(a.prof, K_RETRY, s);
