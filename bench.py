@@ -44,19 +44,32 @@ WORKLOADS = {
 WORKLOAD_DESC = WORKLOADS[WORKLOAD]
 METRIC = "iALS++ epoch throughput (row-block solves/s = (|U|+|I|)*d/b per epoch)"
 
-# DRAM bytes (read + write) per launch of the dominant kernel from the ncu capture summarised
-# in profiles/epoch_kernels_ml20m_136k.md; valid only for the kernel source it was taken on.
-NCU_TRAFFIC = {"sparse": {"source": "paper_2110_14044_gb300/csrc/k_sparse_impl.cuh",
-                          "sha256_16": "b78f768a5a90d9fe", "bytes_per_launch": 177.6e6}}
+# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu capture
+# summarised under profiles/ (per precision); valid only for the kernel sources it
+# was taken on (sha256 of the listed files, concatenated, first 16 hex digits).
+NCU_TRAFFIC = {
+    ("sparse", "bf16"): {"sources": ["paper_2110_14044_gb300/csrc/k_sparse_bf16.cuh",
+                                     "paper_2110_14044_gb300/csrc/k_sparse_impl.cuh"],
+                         "sha256_16": "da96ecf5aec807a1", "bytes_per_launch": 289.2e6},
+    ("sparse", "fp32"): {"sources": ["paper_2110_14044_gb300/csrc/k_sparse_impl.cuh"],
+                         "sha256_16": "8371fb2a2c60dbb9", "bytes_per_launch": 188.7e6},
+}
 
 
-def measured_traffic(kind):
+def sources_hash(paths):
     import hashlib
-    rec = NCU_TRAFFIC.get(kind)
-    if not rec:
+    h = hashlib.sha256()
+    for p in paths:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kind, precision):
+    rec = NCU_TRAFFIC.get((kind, precision))
+    if not rec or not rec["bytes_per_launch"]:
         return None
     try:
-        h = hashlib.sha256(open(os.path.join(ROOT, rec["source"]), "rb").read()).hexdigest()[:16]
+        h = sources_hash(rec["sources"])
     except OSError:
         return None
     return rec["bytes_per_launch"] if h == rec["sha256_16"] else None
@@ -65,6 +78,37 @@ def measured_traffic(kind):
 def env_rank():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
+
+
+# ----------------------------------------------------------------- multi-rank aggregation
+# Under torchrun every rank trains an independent replica (no collective on the
+# data path); the only exchanges are the barriers around the timed region and
+# the maximum of the per-rank times.  These helpers take the device so that the
+# same code runs over NCCL (CUDA tensors) and over gloo (CPU tensors, in tests).
+def rank_barrier(world, device):
+    import torch
+    if device.startswith("cuda"):
+        torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        if device.startswith("cuda"):
+            torch.cuda.synchronize()
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms_max):
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
 
 
 # ----------------------------------------------------------------- clocks
@@ -212,17 +256,7 @@ def run_ours(args):
     rows_per_epoch = (data.n_users + data.n_items) * (prob.d // prob.b)
 
     def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-            torch.cuda.synchronize()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        rank_barrier(world, "cuda")
 
     # warm-up
     for _ in range(args.warmup):
@@ -241,10 +275,10 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    ms = max_over_ranks(ms)
+    ms = max_over_ranks(ms, world, "cuda")
     obj_after = m.objective()
     ms_per_step = ms / args.steps
-    value = world * rows_per_epoch * args.steps / (ms / 1e3)
+    value = job_throughput(rows_per_epoch * args.steps, world, ms)
 
     # per-kernel device times over the same number of eager epochs (events per launch)
     kern, prof_total, _ = _abi.ials_profile_epochs(m.ctx, args.steps)
@@ -264,7 +298,7 @@ def run_ours(args):
     dbytes = work[dom][0] * args.steps  # bytes over all profiled launches
     achieved = dbytes / (dms / 1e3) / 1e9
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": measured_traffic(dom),
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": measured_traffic(dom, args.precision),
                 "peak_source": peak_src,
                 "bytes_per_launch": dbytes / max(dcnt, 1), "ms_per_launch": dms / max(dcnt, 1),
                 "gflops": work[dom][1] * args.steps / (dms / 1e3) / 1e9}
@@ -285,7 +319,7 @@ def run_ours(args):
     e1.record(stream)
     barrier()
     wall = time.perf_counter() - t0
-    e2e_ms = max_over_ranks(max(e0.elapsed_time(e1), wall * 1e3)) / e2e_steps
+    e2e_ms = max_over_ranks(max(e0.elapsed_time(e1), wall * 1e3), world, "cuda") / e2e_steps
     fb = (prob.W0.nbytes + prob.H0.nbytes)
 
     line = {
@@ -304,7 +338,7 @@ def run_ours(args):
         "kernels_ms_per_epoch": {k: v[0] / args.steps for k, v in kern.items()},
         "profiled_epoch_ms": prof_total / args.steps,
         "roofline": roofline,
-        "e2e": {"value": world * rows_per_epoch / (e2e_ms / 1e3), "unit": "rows/s",
+        "e2e": {"value": job_throughput(rows_per_epoch, world, e2e_ms), "unit": "rows/s",
                 "h2d_bytes_per_step": fb, "d2h_bytes_per_step": fb, "ms_per_step": e2e_ms},
         "gpu_launches": int(round(launches_per_epoch * args.steps)),
         "clocks": clk,
@@ -334,7 +368,9 @@ def run_ours(args):
         }
         m2.close()
     if rank == 0 and args.foldin:
-        line["foldin"] = run_foldin()
+        line["foldin"] = run_foldin(cpu_sample=0 if args.no_cpu_baseline else 6)
+    if rank == 0 and args.convergence:
+        line["convergence"] = run_convergence(prob, args.convergence)
     if rank == 0 and args.autotune:
         from paper_2110_14044_gb300 import autotune
         tuned = {}
@@ -348,6 +384,30 @@ def run_ours(args):
     m.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_convergence(prob, epochs):
+    """Objective (Eq. 2, FP64) after each of `epochs` epochs for every admissible
+    block size, in both precisions, from the same initial factors (the analogue,
+    on the training objective, of the paper's quality-vs-b study)."""
+    import paper_2110_14044_gb300 as ials
+    from paper_2110_14044_gb300 import _abi, autotune
+    out = {"epochs": epochs, "desc": "objective after each epoch; same W0, H0 for every run"}
+    for name, prec in (("fp32", _abi.PREC_FP32), ("bf16", _abi.PREC_BF16)):
+        res = {}
+        for b in autotune.CANDIDATES:
+            if not autotune.admissible(prob.d, b, prec):
+                continue
+            m = ials.Model(prob.data, prob.d, b, prob.alpha0, prob.lam, prob.nu, precision=prec,
+                           graph=True, W0=prob.W0, H0=prob.H0)
+            objs = [m.objective()]
+            for _ in range(epochs):
+                m.epoch(1)
+                objs.append(m.objective())
+            res[str(b)] = objs
+            m.close()
+        out[name] = res
+    return out
 
 
 def run_ncu_step(args):
@@ -369,17 +429,33 @@ def run_ncu_step(args):
 
 # ----------------------------------------------------------------- fold-in serving
 FOLDIN_DESC = ("fold-in: frozen H 41,000 x 256 ~ N(0, 0.05^2), b=64, 4 sweeps, alpha0=0.1, "
-               "lambda=1e-3, nu=1; requests arrive Poisson, history lengths log-uniform on "
+               "lambda=1e-3, nu=1; open loop: Poisson arrivals at each rate; closed loop: C "
+               "clients, one request outstanding each; history lengths log-uniform on "
                "[1, 5000] over Zipf(1.0) items; 4 GB workspace")
 
 
-def run_foldin(rates=(2000, 10000, 50000), n_req=3000, seed=0):
-    """Open-loop Poisson arrivals per rate; latency = submit -> result available."""
+def foldin_requests(rng, n_items, n_req, cdf):
+    """History lengths log-uniform on [1, 5000] over Zipf(1.0) items (distinct per request)."""
+    lens = np.exp(rng.uniform(0.0, np.log(5000.0), n_req)).astype(np.int64)
+    reqs = []
+    for n in lens:
+        draw = np.unique(np.minimum(np.searchsorted(cdf, rng.random(2 * n + 8)), n_items - 1))
+        reqs.append(rng.permutation(draw)[:n].astype(np.int32))
+    return reqs
+
+
+def run_foldin(rates=(2000, 5000, 10000, 20000, 50000), n_req=3000, closed_clients=(16, 128),
+               cpu_sample=0, seed=0):
+    """Fold-in serving.  Open loop: Poisson arrivals at each rate, latency = submit ->
+    result in host memory (measured inside the library).  Closed loop: C clients that
+    each submit their next request when the previous result arrives.  Optionally the
+    FP64 oracle's per-request latency on a sample of the same requests (host cores)."""
     import threading
     import paper_2110_14044_gb300 as ials
     from paper_2110_14044_gb300 import _abi
     rng = np.random.Generator(np.random.Philox(key=[seed, 7]))
-    n_items, d = 41000, 256
+    n_items, d, b, sweeps = 41000, 256, 64, 4
+    alpha0, lam, nu = 0.1, 1e-3, 1.0
     H = rng.normal(0.0, 0.05, (n_items, d)).astype(np.float32)
     ranks = np.arange(1, n_items + 1, dtype=np.float64)
     p = ranks ** -1.0
@@ -387,16 +463,12 @@ def run_foldin(rates=(2000, 10000, 50000), n_req=3000, seed=0):
     perm = rng.permutation(n_items)
     cdf = np.cumsum(p[np.argsort(perm)])
     cdf[-1] = 1.0
-    srv = ials.FoldinServer(H, d, 64, 0.1, 1e-3, 1.0, sweeps=4, workspace_bytes=4 << 30)
-    out = {"desc": FOLDIN_DESC, "rates": []}
+    srv = ials.FoldinServer(H, d, b, alpha0, lam, nu, sweeps=sweeps, workspace_bytes=4 << 30)
+    out = {"desc": FOLDIN_DESC, "rates": [], "closed_loop": []}
     for rate in rates:
-        lens = np.exp(rng.uniform(0.0, np.log(5000.0), n_req)).astype(np.int64)
-        reqs = []
-        for n in lens:
-            draw = np.unique(np.minimum(np.searchsorted(cdf, rng.random(2 * n + 8)), n_items - 1))
-            reqs.append(rng.permutation(draw)[:n].astype(np.int32))
-        gaps = rng.exponential(1.0 / rate, n_req)
-        sched = np.cumsum(gaps)
+        reqs = foldin_requests(rng, n_items, n_req, cdf)
+        lens = np.array([r.size for r in reqs])
+        sched = np.cumsum(rng.exponential(1.0 / rate, n_req))
         lat = np.zeros(n_req)
         done_t = np.zeros(n_req)
         tickets = [0] * n_req
@@ -424,13 +496,57 @@ def run_foldin(rates=(2000, 10000, 50000), n_req=3000, seed=0):
                 pass
             tickets[k] = srv.submit(reqs[k])
         th.join()
-        # latency per request is measured inside the library: submission to result in host memory
         span = done_t.max() - t0
         out["rates"].append({"offered_req_s": rate, "achieved_req_s": n_req / span,
                              "p50_ms": float(np.percentile(lat, 50)),
                              "p99_ms": float(np.percentile(lat, 99)), "requests": n_req,
                              "mean_len": float(lens.mean())})
+    for clients in closed_clients:
+        reqs = foldin_requests(rng, n_items, n_req, cdf)
+        lat = np.zeros(n_req)
+        nxt = [0]
+        lock = threading.Lock()
+
+        def client():
+            w = np.empty(d, np.float32)
+            while True:
+                with lock:
+                    k = nxt[0]
+                    nxt[0] += 1
+                if k >= n_req:
+                    return
+                t = srv.submit(reqs[k])
+                while True:
+                    st, us = _abi.ials_foldin_poll_timed(srv.srv, t, w, 2000)
+                    if st == _abi.OK or st == _abi.ENOTPD:
+                        break
+                lat[k] = us / 1e3
+
+        ths = [threading.Thread(target=client) for _ in range(clients)]
+        t0 = time.perf_counter()
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        span = time.perf_counter() - t0
+        out["closed_loop"].append({"clients": clients, "achieved_req_s": n_req / span,
+                                   "p50_ms": float(np.percentile(lat, 50)),
+                                   "p99_ms": float(np.percentile(lat, 99)), "requests": n_req})
     srv.close()
+    if cpu_sample:
+        import oracle
+        reqs = foldin_requests(rng, n_items, cpu_sample, cdf)
+        ms = []
+        for items in reqs:
+            t0 = time.perf_counter()
+            oracle.foldin(H, d, b, alpha0, lam, nu, sweeps, items)
+            ms.append((time.perf_counter() - t0) * 1e3)
+        out["cpu_oracle"] = {"kind": "oracle", "requests": cpu_sample, "cores": 1,
+                             "p50_ms": float(np.percentile(ms, 50)),
+                             "p99_ms": float(np.percentile(ms, 99)),
+                             "mean_len": float(np.mean([r.size for r in reqs])),
+                             "note": "FP64 oracle, one request at a time, one thread; each call "
+                                     "also forms G^I = H^T H (41,000 x 256^2), as the oracle does"}
     return out
 
 
@@ -466,6 +582,8 @@ def main():
                     help="do not run the fold-in serving measurement")
     ap.add_argument("--autotune", action="store_true",
                     help="also time every admissible block size per precision (b sweep)")
+    ap.add_argument("--convergence", type=int, default=0, metavar="E",
+                    help="also record the objective over E epochs for every admissible b")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-step", action="store_true",
