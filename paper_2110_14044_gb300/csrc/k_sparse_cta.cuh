@@ -155,6 +155,151 @@ __device__ void cta_backsolve(const T *M, const T *invd, T *x) {
     }
 }
 
+// FP32 blocked Cholesky of rows 0..B-1 of M (lower part used; row stride SM must
+// be = 4 mod 32 and a multiple of 4) with the right-hand side carried as row B,
+// in panels of 16 columns:
+//  1. the 16 x 16 diagonal block is factorised by warp 0 in registers (lane i
+//     holds row k0 + i; column values are exchanged with shuffles);
+//  2. the rows below it (and row B) are solved against it, x L_11^T = a, one
+//     thread per row, the block read as shared-memory broadcasts;
+//  3. the trailing lower triangle (and row B) is updated, M -= L_21 L_21^T: a
+//     warp takes 8 rows, its lanes columns c, c + 32, ... (16-byte loads of 8
+//     consecutive rows per phase, free of bank conflicts), 8 x 4 panel values
+//     at a time in registers.
+// On return the lower part of rows 0..B-1 holds L, row B holds z = L^{-1} rhs and
+// invd[k] = 1 / L_kk.  A pivot that is not above rel * diag0[k] (or not finite)
+// sets *bad.  All threads of the block call it (blockDim.x >= 128, whole warps).
+template <int B, int SM>
+__device__ void cta_chol16(float *M, float *invd, const float *diag0, int *bad, float rel) {
+    static_assert(B % 16 == 0 && SM % 32 == 4, "panel layout");
+    constexpr int P = 16, NP = B / P;
+    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+#pragma unroll 1
+    for (int p = 0; p < NP; ++p) {
+        const int k0 = P * p;
+        if (warp == 0) {
+            float r[P];
+            const int row = k0 + (lane & (P - 1));
+#pragma unroll
+            for (int j = 0; j < P; j += 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(M + row * SM + k0 + j);
+                r[j] = v.x; r[j + 1] = v.y; r[j + 2] = v.z; r[j + 3] = v.w;
+            }
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const float d = __shfl_sync(kFull, r[k], k);
+                if (lane == k && (!(d > rel * diag0[k0 + k]) || !(d <= 3.0e38f))) *bad = 1;
+                const float inv = rsqrtf(fmaxf(d, 1e-30f));
+                const float lk = r[k] * inv;
+                if (lane == k) invd[k0 + k] = inv;
+                r[k] = lk;
+#pragma unroll
+                for (int j = k + 1; j < P; ++j) r[j] -= lk * __shfl_sync(kFull, lk, j);
+            }
+            if (lane < P) {
+#pragma unroll
+                for (int j = 0; j < P; j += 4)
+                    *reinterpret_cast<float4 *>(M + row * SM + k0 + j) = make_float4(r[j], r[j + 1], r[j + 2], r[j + 3]);
+            }
+        }
+        __syncthreads();
+        const int r0 = k0 + P;
+        for (int i = r0 + tid; i <= B; i += nt) {
+            float x[P];
+#pragma unroll
+            for (int j = 0; j < P; j += 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(M + i * SM + k0 + j);
+                x[j] = v.x; x[j + 1] = v.y; x[j + 2] = v.z; x[j + 3] = v.w;
+            }
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+#pragma unroll
+                for (int m = 0; m < j; ++m) x[j] -= x[m] * M[(k0 + j) * SM + k0 + m];
+                x[j] *= invd[k0 + j];
+            }
+#pragma unroll
+            for (int j = 0; j < P; j += 4)
+                *reinterpret_cast<float4 *>(M + i * SM + k0 + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
+        }
+        __syncthreads();
+        if (r0 < B) {
+            const int nrb = (B + 1 - r0 + 7) / 8;  // 8-row blocks of rows r0..B
+#pragma unroll 1
+            for (int rb = warp; rb < nrb; rb += nw) {
+                const int i0 = r0 + 8 * rb;
+                const int jend = min(i0 + 8, B);           // columns r0 .. jend-1 can be touched
+                const int nc = (jend - r0 + 31) >> 5;      // 32-column groups (<= 4), warp-uniform
+                float out[8][4];
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) out[a][c] = 0.f;
+#pragma unroll
+                for (int m = 0; m < P; m += 4) {
+                    float4 av[8];
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) {
+                        const int i = min(i0 + a, B);
+                        av[a] = *reinterpret_cast<const float4 *>(M + i * SM + k0 + m);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if (c >= nc) break;
+                        const int j = min(r0 + lane + 32 * c, B - 1);
+                        const float4 bv = *reinterpret_cast<const float4 *>(M + j * SM + k0 + m);
+#pragma unroll
+                        for (int a = 0; a < 8; ++a)
+                            out[a][c] += av[a].x * bv.x + av[a].y * bv.y + av[a].z * bv.z + av[a].w * bv.w;
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (c >= nc) break;
+                    const int j = r0 + lane + 32 * c;
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) {
+                        const int i = i0 + a;
+                        if (i <= B && j < B && (j <= i || i == B)) M[i * SM + j] -= out[a][c];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Backward substitution L^T x = z for the factor left by cta_chol16 (z in x on
+// entry), 16-blocks from the bottom: warp 0 solves the block with shuffles, then
+// all threads remove its contribution from the entries above it.
+template <int B, int SM>
+__device__ void cta_backsolve16(const float *M, const float *invd, float *x) {
+    constexpr int P = 16, NP = B / P;
+    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
+#pragma unroll 1
+    for (int p = NP - 1; p >= 0; --p) {
+        const int k0 = P * p;
+        if (warp == 0) {
+            const int m = lane & (P - 1);
+            float z = x[k0 + m];
+#pragma unroll
+            for (int j = P - 1; j >= 0; --j) {
+                const float xj = __shfl_sync(kFull, z * invd[k0 + j], j);
+                if (m < j) z -= M[(k0 + j) * SM + k0 + m] * xj;
+                else if (m == j) z = xj;
+            }
+            if (lane < P) x[k0 + m] = z;
+        }
+        __syncthreads();
+        for (int q = tid; q < k0; q += nt) {
+            float v = x[q];
+#pragma unroll
+            for (int j = 0; j < P; ++j) v -= M[(k0 + j) * SM + q] * x[k0 + j];
+            x[q] = v;
+        }
+        __syncthreads();
+    }
+}
+
 // Adds alpha0 G_pipi + lambda I to rows 0..B-1 of M (lower part) and R_r to row B;
 // records the diagonal in diag0.
 template <int B, int SM, typename T>
@@ -209,6 +354,49 @@ __device__ void cta_residual_update(const StepArgs &a, int64_t s0, int len, cons
             }
         }
         __syncthreads();
+    }
+}
+
+// Residual update after the solve, using what the accumulation left staged: the
+// last two chunks of the row are still in the two staging buffers (chunk ch in
+// buffer ch & 1), so they are used first; chunks 0 .. nch-3 are gathered again,
+// double-buffered.  One warp per interaction, lanes splitting b.
+template <int B, bool PERM>
+__device__ void cta_residual_update2(const StepArgs &a, int64_t s0, int len, int nch, const float *x,
+                                     float *buf0) {
+    constexpr int CH = CtaCfg<B>::CH, SB = CtaCfg<B>::SB, BUF = CtaCfg<B>::BUF;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    float xr[B / 32];
+#pragma unroll
+    for (int m = 0; m < B / 32; ++m) xr[m] = x[lane + 32 * m];
+    auto process = [&](int ch, const float *bp) {
+        const int cnt = min(CH, len - ch * CH);
+        for (int k = warp; k < cnt; k += nw) {
+            float t = 0.f;
+#pragma unroll
+            for (int m = 0; m < B / 32; ++m) t += xr[m] * bp[k * SB + lane + 32 * m];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+            if (lane == 0) {
+                const int64_t s = s0 + (int64_t)ch * CH + k;
+                const int64_t q = PERM ? (int64_t)a.pos[s] : s;
+                a.e[q] -= t;
+            }
+        }
+    };
+    for (int ch = nch - 1; ch >= 0 && ch >= nch - 2; --ch) process(ch, buf0 + (ch & 1) * BUF);
+    if (nch <= 2) return;
+    __syncthreads();  // the staged chunks are consumed before they are overwritten
+    cta_gather<B>(a, s0, CH, buf0);
+    cp_async_commit();
+    for (int ch = 0; ch <= nch - 3; ++ch) {
+        cp_async_wait_all();
+        __syncthreads();
+        if (ch + 1 <= nch - 3) {
+            cta_gather<B>(a, s0 + (int64_t)(ch + 1) * CH, CH, buf0 + ((ch + 1) & 1) * BUF);
+            cp_async_commit();
+        }
+        process(ch, buf0 + (ch & 1) * BUF);
     }
 }
 
@@ -322,7 +510,7 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_sparse_cta(const StepArg
         if (tid == 0) flag[1] = a.force_fp64 ? 1 : 0;
         cta_dense_terms<B, SB, float>(a, M, diag0, tk.row, lam);
         __syncthreads();
-        cta_cholesky<B, SB, float>(M, invd, diag0, &flag[1], 1e-5f);
+        cta_chol16<B, SB>(M, invd, diag0, &flag[1], 1e-5f);
         if (flag[1]) {  // CTA-uniform: queue the row for the FP64 re-solve
             if (tid == 0) {
                 const int i = atomicAdd(a.retry, 1);
@@ -332,7 +520,7 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_sparse_cta(const StepArg
         }
         for (int j = tid; j < B; j += blockDim.x) xv[j] = M[B * SB + j];
         __syncthreads();
-        cta_backsolve<B, SB, float>(M, invd, xv);
+        cta_backsolve16<B, SB>(M, invd, xv);
         bool finite = true;
         for (int j = 0; j < B; ++j) finite = finite && isfinite(xv[j]);
         if (!finite) {
@@ -343,7 +531,7 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_sparse_cta(const StepArg
             continue;
         }
         for (int j = tid; j < B; j += blockDim.x) apply_delta(a.X, a.Xh, a.Xl, (int64_t)tk.row * a.d + a.p0 + j, xv[j]);
-        cta_residual_update<B, PERM>(a, tk.begin, tk.len, xv, buf0);
+        cta_residual_update2<B, PERM>(a, tk.begin, tk.len, nch, xv, buf0);
     }
 }
 
@@ -374,12 +562,12 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_split_solve_cta(const St
         const float lam = a.lambda * (1.0f + a.nu * (float)sr.len);
         cta_dense_terms<B, SB, float>(a, M, diag0, sr.row, lam);
         __syncthreads();
-        cta_cholesky<B, SB, float>(M, invd, diag0, &flag[1], 1e-5f);
+        cta_chol16<B, SB>(M, invd, diag0, &flag[1], 1e-5f);
         bool ok = !flag[1];
         if (ok) {
             for (int j = tid; j < B; j += blockDim.x) xv[j] = M[B * SB + j];
             __syncthreads();
-            cta_backsolve<B, SB, float>(M, invd, xv);
+            cta_backsolve16<B, SB>(M, invd, xv);
             for (int j = 0; j < B; ++j) ok = ok && isfinite(xv[j]);
         }
         if (!ok) {
