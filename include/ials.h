@@ -60,8 +60,9 @@ enum {
     IALS_PREC_FP32 = 0,  /* FP32 everywhere (FP64 objective, FP64 retry of failed pivots) */
     IALS_PREC_BF16 = 1   /* BF16 tensor-core statistics: x = hi + lo split into two bf16,
                           * products hi*hi + hi*lo + lo*hi accumulated in FP32 (about 16
-                          * bits); FP32 Cholesky with FP64 retry, FP64 objective.  Needs
-                          * b = 16 or 32, d % 8 == 0 and unweighted data (alpha NULL). */
+                          * bits); FP32 solve with FP64 retry, FP64 objective.  Needs
+                          * b in {16, 32, 64, 128}, d % 8 == 0 and unweighted data
+                          * (alpha NULL). */
 };
 
 /* ials_params.flags */
@@ -176,7 +177,8 @@ ials_status ials_partial_gramian(const float *X, int64_t n, int32_t d, int32_t p
 
 /* Partial Gramian on the tcgen05 tensor cores (Eq. 10): X is split into BF16
  * hi/lo halves and G = Xh^T Xh_pi + Xh^T Xl_pi + Xl^T Xh_pi is accumulated in
- * FP32 (about 16 bits).  Needs d % 8 == 0, bs in {16, 32}, p0 % 8 == 0.
+ * FP32 (about 16 bits).  Needs d % 8 == 0, bs in {16, 32, 64, 128}, p0 % 8 == 0
+ * (blocks wider than 32 columns are formed 32 columns at a time).
  * X (n x d float32) and G (d x bs float32) are device arrays; temporaries are
  * allocated per call.  Synchronous.  IALS_ETIMEDOUT if a bounded device wait
  * gave up. */

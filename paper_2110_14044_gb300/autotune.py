@@ -23,7 +23,7 @@ def admissible(d: int, b: int, precision: int) -> bool:
     if d % b != 0 or b > d:
         return False
     if precision == _abi.PREC_BF16:
-        return b in (16, 32) and d % 8 == 0
+        return b in (16, 32, 64, 128) and d % 8 == 0
     return b in (1, 2, 4, 8, 16, 32, 64, 128)
 
 

@@ -230,6 +230,16 @@ cudaError_t residual_enqueue(ials_ctx *c) {
                                  c->p.d, c->e, c->ctl, c->stream);
 }
 
+cudaError_t launch_sparse_bf16(int32_t b, const StepArgs &a, cudaStream_t s) {
+    switch (b) {
+        case 16: return launch_sparse_bf16_b16(a, s);
+        case 32: return launch_sparse_bf16_b32(a, s);
+        case 64: return launch_sparse_bf16_b64(a, s);
+        case 128: return launch_sparse_bf16_b128(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 ials_status step_enqueue(ials_ctx *c, int side, int block, Profiler *prof = nullptr) {
     const int32_t d = c->p.d, b = c->p.b, p0 = block * b;
     SideDev &sd = c->side[side];
@@ -291,8 +301,7 @@ ials_status step_enqueue(ials_ctx *c, int side, int block, Profiler *prof = null
     a.Fh = side == 0 ? c->Hh : c->Wh;
     a.Fl = side == 0 ? c->Hl : c->Wl;
     if (c->p.precision == IALS_PREC_BF16) {
-        IALS_CUDA(b == 16 ? launch_sparse_bf16_b16(a, s) : launch_sparse_bf16_b32(a, s),
-                  "sparse block step (BF16)");
+        IALS_CUDA(launch_sparse_bf16(b, a, s), "sparse block step (BF16)");
     } else {
         IALS_CUDA(launch_sparse(a, s), "sparse block step");
     }
@@ -375,8 +384,9 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
         return fail(IALS_EINVAL, "alpha0, lambda, nu must be finite and >= 0");
     if (p.precision != IALS_PREC_FP32 && p.precision != IALS_PREC_BF16)
         return fail(IALS_EINVAL, "unknown precision");
-    if (p.precision == IALS_PREC_BF16 && ((p.b != 16 && p.b != 32) || p.d % 8 != 0 || alpha))
-        return fail(IALS_EINVAL, "BF16 precision needs b = 16 or 32, d % 8 == 0 and unweighted data");
+    if (p.precision == IALS_PREC_BF16 &&
+        ((p.b != 16 && p.b != 32 && p.b != 64 && p.b != 128) || p.d % 8 != 0 || alpha))
+        return fail(IALS_EINVAL, "BF16 precision needs b in {16, 32, 64, 128}, d % 8 == 0 and unweighted data");
     if (n_users <= 0 || n_items <= 0) return fail(IALS_EINVAL, "n_users and n_items must be > 0");
     if (nnz < 0 || nnz >= (int64_t)1 << 31) return fail(IALS_EINVAL, "nnz must be in [0, 2^31)");
     if (!u_indptr || (nnz > 0 && !u_items)) return fail(IALS_EINVAL, "user CSR missing");
@@ -585,7 +595,7 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
         e7 = cudaMemsetAsync(c->ctl, 0, 2 * sizeof(int32_t), c->stream);
         if (e7 == cudaSuccess) {
             if (p.precision == IALS_PREC_BF16)
-                e7 = b == 16 ? launch_sparse_bf16_b16(a, c->stream) : launch_sparse_bf16_b32(a, c->stream);
+                e7 = launch_sparse_bf16(b, a, c->stream);
             else
                 e7 = launch_sparse(a, c->stream);
         }
@@ -773,9 +783,9 @@ ials_status ials_work_model(ials_ctx *c, double *bytes, double *flops, int32_t n
 
 ials_status ials_partial_gramian_bf16(const float *X, int64_t n, int32_t d, int32_t p0, int32_t bs,
                                       float *G, void *cuda_stream) {
-    if (!X || !G || n < 0 || d < 8 || d % 8 != 0 || (bs != 16 && bs != 32) || p0 < 0 || p0 % 8 != 0 ||
-        p0 + bs > d)
-        return fail(IALS_EINVAL, "bad BF16 Gramian arguments (d % 8 == 0, bs in {16, 32}, p0 % 8 == 0)");
+    if (!X || !G || n < 0 || d < 8 || d % 8 != 0 || (bs != 16 && bs != 32 && bs != 64 && bs != 128) || p0 < 0 ||
+        p0 % 8 != 0 || p0 + bs > d)
+        return fail(IALS_EINVAL, "bad BF16 Gramian arguments (d % 8 == 0, bs in {16, 32, 64, 128}, p0 % 8 == 0)");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const int64_t count = n * (int64_t)d;
     const int64_t wsn = std::max<int64_t>(gram_tc_ws_floats(n, d, bs), 1);

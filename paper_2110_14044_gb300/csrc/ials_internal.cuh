@@ -173,6 +173,10 @@ cudaError_t launch_gram_reduce(const float *ws, int nsplit, int64_t count, float
 struct alignas(64) GramMaps {
     unsigned char ah[128], al[128], bh[128], bl[128];
 };
+// Columns col0 .. col0+cols-1 of G (row stride ldg) = fixed-order sum of nsplit
+// partial rows x cols blocks.
+cudaError_t launch_gram_reduce_cols(const float *ws, int nsplit, int32_t rows, int32_t cols, float *G, int32_t ldg,
+                                    int32_t col0, cudaStream_t s);
 bool make_gram_maps(GramMaps &g, const __nv_bfloat16 *hi, const __nv_bfloat16 *lo, int64_t rows, int32_t d,
                     int32_t b);
 int64_t gram_tc_ws_floats(int64_t n, int32_t d, int32_t bs);
@@ -217,5 +221,7 @@ int64_t foldin_factor_floats(int32_t d, int32_t b);
 // BF16 mode (k_sparse_bf16.cu): tensor-core statistics for block sizes 16 and 32
 cudaError_t launch_sparse_bf16_b16(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_sparse_bf16_b32(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_sparse_bf16_b64(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_sparse_bf16_b128(const StepArgs &a, cudaStream_t s);
 
 }  // namespace ials

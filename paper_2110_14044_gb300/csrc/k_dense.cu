@@ -612,6 +612,25 @@ cudaError_t launch_gram_capped(const float *X, int64_t n, int32_t d, int32_t p0,
     return cudaGetLastError();
 }
 
+// Fixed-order sum of nsplit partial rows x cols blocks into columns col0 .. col0+cols-1
+// of G (row stride ldg).
+__global__ void k_gram_reduce_cols(const float *__restrict__ ws, int32_t nsplit, int32_t rows, int32_t cols,
+                                   float *__restrict__ G, int32_t ldg, int32_t col0) {
+    const int64_t count = (int64_t)rows * cols;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float t = 0.f;
+    for (int s = 0; s < nsplit; ++s) t += ws[(int64_t)s * count + i];
+    G[(i / cols) * ldg + col0 + (i % cols)] = t;
+}
+
+cudaError_t launch_gram_reduce_cols(const float *ws, int nsplit, int32_t rows, int32_t cols, float *G, int32_t ldg,
+                                    int32_t col0, cudaStream_t s) {
+    const int64_t count = (int64_t)rows * cols;
+    k_gram_reduce_cols<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(ws, nsplit, rows, cols, G, ldg, col0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gram_reduce(const float *ws, int nsplit, int64_t count, float *G, cudaStream_t s) {
     k_gram_reduce<float><<<(unsigned)((count + 255) / 256), 256, 0, s>>>(ws, nsplit, count, G);
     return cudaGetLastError();

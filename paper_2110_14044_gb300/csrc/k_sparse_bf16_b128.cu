@@ -1,0 +1,8 @@
+// Block size 128 instantiation of the BF16 tensor-core sparse block step (see k_sparse_cta_bf16.cuh).
+#include "k_sparse_cta_bf16.cuh"
+
+namespace ials {
+cudaError_t launch_sparse_bf16_b128(const StepArgs &a, cudaStream_t s) {
+    return a.pos ? launch_sparse_cta_bf16_all<128, true>(a, s) : launch_sparse_cta_bf16_all<128, false>(a, s);
+}
+}  // namespace ials

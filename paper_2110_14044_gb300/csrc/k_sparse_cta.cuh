@@ -400,8 +400,9 @@ __device__ void cta_residual_update2(const StepArgs &a, int64_t s0, int len, int
     }
 }
 
+// Two resident CTAs per SM at B = 128 (registers capped at 96), three at B = 64.
 template <int B, bool PERM, bool HAS_A>
-__global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_sparse_cta(const StepArgs a) {
+__global__ void __launch_bounds__(CtaCfg<B>::THREADS, B == 64 ? 3 : 2) k_sparse_cta(const StepArgs a) {
     using C = CtaCfg<B>;
     constexpr int SB = C::SB, CH = C::CH;
     extern __shared__ float4 smem4[];
@@ -420,12 +421,14 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_sparse_cta(const StepArg
     const int kstart = active ? grp : C::CH;  // idle threads skip the accumulation
     int ti = 0, tj = 0;
     tri_index(tid % C::NTL, ti, tj);
+    // the next task index is fetched while the current task runs
+    if (tid == 0) flag[0] = atomicAdd(a.counter, 1);
     for (;;) {
-        __syncthreads();
-        if (tid == 0) flag[0] = atomicAdd(a.counter, 1);
         __syncthreads();
         const int tsk = flag[0];
         if (tsk >= a.n_tasks) break;
+        __syncthreads();  // every thread has read flag[0]
+        if (tid == 0) flag[0] = atomicAdd(a.counter, 1);
         const Task tk = a.tasks[tsk];
         const int nch = (tk.len + CH - 1) / CH;
         float acc[8][8], gacc[8];

@@ -247,7 +247,8 @@ __global__ void __launch_bounds__(128, 1)
     k_tc_rowterm(const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
                  const __grid_constant__ CUtensorMap mGh, const __grid_constant__ CUtensorMap mGl,
                  const float *__restrict__ X, const int64_t *__restrict__ ptr, int32_t n_rows, int32_t d,
-                 int32_t p0, float alpha0, float lambda, float nu, float *__restrict__ R, int32_t *err) {
+                 int32_t p0, float alpha0, float lambda, float nu, float *__restrict__ R, int32_t ldr,
+                 int32_t *err) {
     using C = TcRowCfg<N>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(128, 1)
     if (row < n_rows && ok) {
         const float lam = lambda * (1.0f + nu * (float)(ptr[row + 1] - ptr[row]));
         const float *x = X + (int64_t)row * d + p0;
-        float *out = R + (int64_t)row * N;
+        float *out = R + (int64_t)row * ldr;
 #pragma unroll
         for (int f = 0; f < N; f += 4) {
             const float4 xv = *reinterpret_cast<const float4 *>(x + f);
@@ -357,13 +358,13 @@ __global__ void __launch_bounds__(128, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;\n" ::"r"(tmem) : "memory");
 }
 
-// G (d x b, FP32) -> G^T hi and lo (b x d, BF16)
-__global__ void k_transpose_split(const float *__restrict__ G, int32_t d, int32_t b, __nv_bfloat16 *__restrict__ th,
-                                  __nv_bfloat16 *__restrict__ tl) {
+// Columns col0 .. col0+b-1 of G (d x ldg, FP32) -> their transpose, hi and lo (b x d, BF16)
+__global__ void k_transpose_split(const float *__restrict__ G, int32_t ldg, int32_t col0, int32_t d, int32_t b,
+                                  __nv_bfloat16 *__restrict__ th, __nv_bfloat16 *__restrict__ tl) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d * b) return;
     const int f = i / d, k = i % d;
-    const float x = G[(int64_t)k * b + f];
+    const float x = G[(int64_t)k * ldg + col0 + f];
     const __nv_bfloat16 h = __float2bfloat16_rn(x);
     th[i] = h;
     tl[i] = __float2bfloat16_rn(x - __bfloat162float(h));
@@ -417,9 +418,14 @@ int tc_splits(int64_t n, int32_t d, int &kper) {
 
 // Tensor maps of one BF16 hi/lo pair for the tcgen05 Gramian: A boxes
 // (64 coordinates x 64 rows, 128B swizzle) and B boxes (b coordinates x 64 rows).
+// Blocks wider than 32 columns (b = 64, 128) are processed as 32-column slabs:
+// the accumulator holds 32 TMEM columns.
+static int tc_slab(int32_t b) { return b <= 32 ? b : 32; }
+
 bool make_gram_maps(GramMaps &g, const __nv_bfloat16 *hi, const __nv_bfloat16 *lo, int64_t rows, int32_t d,
-                    int32_t b) {
-    if (d % 8 != 0 || (b != 16 && b != 32)) return false;  // the accumulator holds 32 TMEM columns
+                    int32_t b_full) {
+    const int32_t b = tc_slab(b_full);
+    if (d % 8 != 0 || (b != 16 && b != 32) || b_full % b != 0) return false;
     const CUtensorMapSwizzle bsw = b == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
                                            : (b == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
     static_assert(sizeof(CUtensorMap) == sizeof(g.ah), "tensor map size");
@@ -430,8 +436,9 @@ bool make_gram_maps(GramMaps &g, const __nv_bfloat16 *hi, const __nv_bfloat16 *l
 }
 
 bool make_row_maps(RowMaps &m, const __nv_bfloat16 *xh, const __nv_bfloat16 *xl, int64_t rows, int32_t d,
-                   const __nv_bfloat16 *gth, const __nv_bfloat16 *gtl, int32_t b) {
-    if (d % 8 != 0 || (b != 16 && b != 32)) return false;
+                   const __nv_bfloat16 *gth, const __nv_bfloat16 *gtl, int32_t b_full) {
+    const int32_t b = tc_slab(b_full);
+    if (d % 8 != 0 || (b != 16 && b != 32) || b_full % b != 0) return false;
     static_assert(sizeof(CUtensorMap) == sizeof(m.xh), "tensor map size");
     return encode_2d(reinterpret_cast<CUtensorMap *>(m.xh), xh, rows, d, 64, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
            encode_2d(reinterpret_cast<CUtensorMap *>(m.xl), xl, rows, d, 64, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
@@ -443,35 +450,38 @@ cudaError_t launch_rowterm_tc(const RowMaps &m, const float *G, __nv_bfloat16 *g
                               const float *X, const int64_t *ptr, int32_t n_rows, int32_t d, int32_t p0, int32_t b,
                               float alpha0, float lambda, float nu, float *R, int32_t *err, cudaStream_t s) {
     if (n_rows == 0) return cudaSuccess;
-    k_transpose_split<<<(d * b + 255) / 256, 256, 0, s>>>(G, d, b, gth, gtl);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    const int32_t bs = tc_slab(b);
+    if ((bs != 16 && bs != 32) || b % bs != 0) return cudaErrorInvalidValue;
     const CUtensorMap *xh = reinterpret_cast<const CUtensorMap *>(m.xh);
     const CUtensorMap *xl = reinterpret_cast<const CUtensorMap *>(m.xl);
     const CUtensorMap *gh = reinterpret_cast<const CUtensorMap *>(m.gh);
     const CUtensorMap *gl = reinterpret_cast<const CUtensorMap *>(m.gl);
     const int grid = (n_rows + 127) / 128;
     static bool a16 = false, a32 = false;
-    if (b == 16) {
-        if (!a16) {
-            e = cudaFuncSetAttribute(k_tc_rowterm<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcRowCfg<16>::SMEM);
-            if (e != cudaSuccess) return e;
-            a16 = true;
-        }
-        k_tc_rowterm<16><<<grid, 128, TcRowCfg<16>::SMEM, s>>>(*xh, *xl, *gh, *gl, X, ptr, n_rows, d, p0, alpha0,
-                                                               lambda, nu, R, err);
-    } else if (b == 32) {
-        if (!a32) {
-            e = cudaFuncSetAttribute(k_tc_rowterm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcRowCfg<32>::SMEM);
-            if (e != cudaSuccess) return e;
-            a32 = true;
-        }
-        k_tc_rowterm<32><<<grid, 128, TcRowCfg<32>::SMEM, s>>>(*xh, *xl, *gh, *gl, X, ptr, n_rows, d, p0, alpha0,
-                                                               lambda, nu, R, err);
-    } else {
-        return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    if (bs == 16 && !a16) {
+        e = cudaFuncSetAttribute(k_tc_rowterm<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcRowCfg<16>::SMEM);
+        if (e != cudaSuccess) return e;
+        a16 = true;
     }
-    return cudaGetLastError();
+    if (bs == 32 && !a32) {
+        e = cudaFuncSetAttribute(k_tc_rowterm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcRowCfg<32>::SMEM);
+        if (e != cudaSuccess) return e;
+        a32 = true;
+    }
+    // one slab of bs columns at a time: its G^T columns, then R[:, c0 : c0 + bs]
+    for (int32_t c0 = 0; c0 < b; c0 += bs) {
+        k_transpose_split<<<(d * bs + 255) / 256, 256, 0, s>>>(G, b, c0, d, bs, gth, gtl);
+        if (bs == 16)
+            k_tc_rowterm<16><<<grid, 128, TcRowCfg<16>::SMEM, s>>>(*xh, *xl, *gh, *gl, X, ptr, n_rows, d, p0 + c0,
+                                                                   alpha0, lambda, nu, R + c0, b, err);
+        else
+            k_tc_rowterm<32><<<grid, 128, TcRowCfg<32>::SMEM, s>>>(*xh, *xl, *gh, *gl, X, ptr, n_rows, d, p0 + c0,
+                                                                   alpha0, lambda, nu, R + c0, b, err);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 int64_t gram_tc_ws_floats(int64_t n, int32_t d, int32_t bs) {
@@ -479,10 +489,12 @@ int64_t gram_tc_ws_floats(int64_t n, int32_t d, int32_t bs) {
     return (int64_t)tc_splits(n, d, kper) * d * bs;
 }
 
-cudaError_t launch_gram_tc(const GramMaps &g, int64_t n, int32_t d, int32_t p0, int32_t bs, float *G, float *ws,
+cudaError_t launch_gram_tc(const GramMaps &g, int64_t n, int32_t d, int32_t p0, int32_t b, float *G, float *ws,
                            int32_t *err, cudaStream_t s) {
-    const int64_t count = (int64_t)d * bs;
+    const int64_t count = (int64_t)d * b;
     if (n == 0) return cudaMemsetAsync(G, 0, sizeof(float) * count, s);
+    const int32_t bs = tc_slab(b);
+    if ((bs != 16 && bs != 32) || b % bs != 0) return cudaErrorInvalidValue;
     int kper = 0;
     const int ns = tc_splits(n, d, kper);
     const dim3 grid((d + TC_M - 1) / TC_M, ns);
@@ -492,30 +504,29 @@ cudaError_t launch_gram_tc(const GramMaps &g, int64_t n, int32_t d, int32_t p0, 
     const CUtensorMap *bl = reinterpret_cast<const CUtensorMap *>(g.bl);
     static bool attr16 = false, attr32 = false;
     cudaError_t e = cudaSuccess;
-    switch (bs) {
-        case 16:
-            if (!attr16) {
-                e = cudaFuncSetAttribute(k_tc_gram<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcGramCfg<16>::SMEM);
-                attr16 = e == cudaSuccess;
-            }
-            if (e == cudaSuccess)
-                k_tc_gram<16><<<grid, 128, TcGramCfg<16>::SMEM, s>>>(*ah, *al, *bh, *bl, n, d, p0, bs, kper, ws, err);
-            break;
-        case 32:
-            if (!attr32) {
-                e = cudaFuncSetAttribute(k_tc_gram<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcGramCfg<32>::SMEM);
-                attr32 = e == cudaSuccess;
-            }
-            if (e == cudaSuccess)
-                k_tc_gram<32><<<grid, 128, TcGramCfg<32>::SMEM, s>>>(*ah, *al, *bh, *bl, n, d, p0, bs, kper, ws, err);
-            break;
-        default:
-            return cudaErrorInvalidValue;
+    if (bs == 16 && !attr16) {
+        e = cudaFuncSetAttribute(k_tc_gram<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcGramCfg<16>::SMEM);
+        if (e != cudaSuccess) return e;
+        attr16 = true;
     }
-    if (e != cudaSuccess) return e;
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_gram_reduce(ws, ns, count, G, s);
+    if (bs == 32 && !attr32) {
+        e = cudaFuncSetAttribute(k_tc_gram<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcGramCfg<32>::SMEM);
+        if (e != cudaSuccess) return e;
+        attr32 = true;
+    }
+    // one slab of bs columns at a time (split-K partials, then a fixed-order
+    // reduce into columns c0 .. c0 + bs - 1 of G)
+    for (int32_t c0 = 0; c0 < b; c0 += bs) {
+        if (bs == 16)
+            k_tc_gram<16><<<grid, 128, TcGramCfg<16>::SMEM, s>>>(*ah, *al, *bh, *bl, n, d, p0 + c0, bs, kper, ws, err);
+        else
+            k_tc_gram<32><<<grid, 128, TcGramCfg<32>::SMEM, s>>>(*ah, *al, *bh, *bl, n, d, p0 + c0, bs, kper, ws, err);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = launch_gram_reduce_cols(ws, ns, d, bs, G, b, c0, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace ials

@@ -59,16 +59,16 @@ def test_bf16_epochs_within_objective_tolerance(d, b):
     assert rel_embed_err(W, Wr) <= 5e-2 and rel_embed_err(H, Hr) <= 5e-2
 
 
-@pytest.mark.parametrize("b", [16, 32])
+@pytest.mark.parametrize("b", [16, 32, 64, 128])
 def test_bf16_block_steps(b):
-    d = 64
+    d = 64 if b <= 32 else 128
     prob = synth.preset("parity_2k", seed=b, n_users=300, n_items=200, nnz=6000, len_max=200, d=d)
     data = prob.data
     m = Model(data, d, b, 0.1, 2e-3, 0.3, W0=prob.W0, H0=prob.H0)
     P = oracle.Problem.from_data(data, d, b, 0.1, 2e-3, 0.3)
     W, H = P.factors(prob.W0, prob.H0)
     yhat = oracle.predict(P, W, H)
-    for k in range(2):
+    for k in range(min(2, d // b)):
         for side in (0, 1):
             assert m.block_step(side, k) == 0
             oracle.halfstep(P, side, k, W, H, yhat)
@@ -101,6 +101,34 @@ def test_bf16_long_rows_and_determinism():
     assert abs(runs[0][0] - ref) / ref <= BF16_OBJ_TOL
 
 
+@pytest.mark.parametrize("b", [64, 128])
+def test_bf16_large_blocks_long_rows_and_epochs(b):
+    """CTA kernels (b = 64, 128): rows cut into chunks, graph replay, objective vs the oracle."""
+    n_users, n_items, d = 500, 400, 128
+    rng = np.random.default_rng(b)
+    mask = rng.random((n_users, n_items)) < 0.04
+    mask[3, :] = True        # a long user row
+    mask[:, 11] = True       # a long item row
+    u, i = np.nonzero(mask)
+    data = synth.from_pairs(n_users, n_items, u, i)
+    W0, H0 = synth.init_factors(n_users, n_items, d, 0.1 / np.sqrt(d), b)
+    runs = []
+    for graph in (False, True):
+        m = Model(data, d, b, 0.1, 1e-3, 0.3, W0=W0, H0=H0, graph=graph)
+        o, st = m.epoch(2, objective=True)
+        assert st == 0
+        runs.append((o, *m.factors()))
+    np.testing.assert_array_equal(runs[0][1], runs[1][1])
+    np.testing.assert_array_equal(runs[0][2], runs[1][2])
+    P = oracle.Problem.from_data(data, d, b, 0.1, 1e-3, 0.3)
+    Wr, Hr, _, _, _ = oracle.ialspp(P, 2, W0, H0)
+    ref = oracle.objective(P, Wr, Hr)
+    print(f"b={b}: objective rel err {abs(runs[0][0] - ref) / ref:.2e}, "
+          f"embedding W {rel_embed_err(runs[0][1], Wr):.2e} H {rel_embed_err(runs[0][2], Hr):.2e}")
+    assert abs(runs[0][0] - ref) / ref <= BF16_OBJ_TOL
+    assert rel_embed_err(runs[0][1], Wr) <= 5e-2 and rel_embed_err(runs[0][2], Hr) <= 5e-2
+
+
 def test_bf16_fp64_retry_updates_shadows():
     prob = synth.preset("parity_2k", seed=7, n_users=300, n_items=200, nnz=6000, len_max=200, d=32, b=16)
     a = Model(prob.data, 32, 16, 0.1, 1e-3, W0=prob.W0, H0=prob.H0)
@@ -123,7 +151,8 @@ def test_bf16_rejects_unsupported_inputs():
 
 @pytest.mark.parametrize("n,d,p0,bs", [(1, 8, 0, 16), (64, 128, 32, 32), (1000, 64, 48, 16),
                                        (20011, 128, 96, 32), (136000, 128, 0, 32), (5000, 256, 224, 32),
-                                       (3000, 1024, 512, 32)])
+                                       (3000, 1024, 512, 32), (5000, 256, 64, 64), (20011, 128, 0, 128),
+                                       (3000, 1024, 896, 128)])
 def test_tcgen05_gramian(n, d, p0, bs):
     """tcgen05 Gramian (BF16 hi/lo, FP32 accumulate) against FP64 numpy."""
     import torch
