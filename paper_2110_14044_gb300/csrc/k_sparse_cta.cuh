@@ -400,9 +400,9 @@ __device__ void cta_residual_update2(const StepArgs &a, int64_t s0, int len, int
     }
 }
 
-// Two resident CTAs per SM at B = 128 (registers capped at 96), three at B = 64.
+// Two resident CTAs per SM (at B = 128 registers are capped at 96).
 template <int B, bool PERM, bool HAS_A>
-__global__ void __launch_bounds__(CtaCfg<B>::THREADS, B == 64 ? 3 : 2) k_sparse_cta(const StepArgs a) {
+__global__ void __launch_bounds__(CtaCfg<B>::THREADS, 2) k_sparse_cta(const StepArgs a) {
     using C = CtaCfg<B>;
     constexpr int SB = C::SB, CH = C::CH;
     extern __shared__ float4 smem4[];
@@ -437,6 +437,21 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS, B == 64 ? 3 : 2) k_sparse_
             gacc[i] = 0.f;
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        }
+        const float lam = a.lambda * (1.0f + a.nu * (float)tk.len);
+        if (tk.slot < 0 && grp == 0) {  // whole row: group 0 starts from alpha0 G_pipi + lambda_r I and R_r
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float *gr = a.G + (int64_t)(a.p0 + 8 * ti + i) * B + 8 * tj;
+                const float4 g0 = *reinterpret_cast<const float4 *>(gr);
+                const float4 g1 = *reinterpret_cast<const float4 *>(gr + 4);
+                acc[i][0] = a.alpha0 * g0.x; acc[i][1] = a.alpha0 * g0.y;
+                acc[i][2] = a.alpha0 * g0.z; acc[i][3] = a.alpha0 * g0.w;
+                acc[i][4] = a.alpha0 * g1.x; acc[i][5] = a.alpha0 * g1.y;
+                acc[i][6] = a.alpha0 * g1.z; acc[i][7] = a.alpha0 * g1.w;
+                if (ti == tj) acc[i][i] += lam;
+                if (tj == 0) gacc[i] = a.R[(int64_t)tk.row * B + 8 * ti + i];
+            }
         }
         auto meta = [&](int j, int bi) {  // residual and weight of chunk j into buffer bi (warp 0)
             const int cnt = min(CH, tk.len - j * CH);
@@ -509,9 +524,8 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS, B == 64 ? 3 : 2) k_sparse_
             for (int j = tid; j < B; j += blockDim.x) P[B * B + j] = M[B * SB + j];
             continue;
         }
-        const float lam = a.lambda * (1.0f + a.nu * (float)tk.len);
         if (tid == 0) flag[1] = a.force_fp64 ? 1 : 0;
-        cta_dense_terms<B, SB, float>(a, M, diag0, tk.row, lam);
+        for (int i = tid; i < B; i += blockDim.x) diag0[i] = M[i * SB + i];  // the dense terms are in already
         __syncthreads();
         cta_chol16<B, SB>(M, invd, diag0, &flag[1], 1e-5f);
         if (flag[1]) {  // CTA-uniform: queue the row for the FP64 re-solve
@@ -524,9 +538,7 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS, B == 64 ? 3 : 2) k_sparse_
         for (int j = tid; j < B; j += blockDim.x) xv[j] = M[B * SB + j];
         __syncthreads();
         cta_backsolve16<B, SB>(M, invd, xv);
-        bool finite = true;
-        for (int j = 0; j < B; ++j) finite = finite && isfinite(xv[j]);
-        if (!finite) {
+        if (!__syncthreads_and(tid >= B || isfinite(xv[tid]))) {
             if (tid == 0) {
                 const int i = atomicAdd(a.retry, 1);
                 a.retry[1 + i] = tk.row;

@@ -10,8 +10,9 @@
 // MT + 1 tiles, so every warp does the same number of products.  Each warp's
 // tile list is fixed at compile time (the kernel dispatches on the warp index),
 // which keeps its fragments and accumulators in registers; a warp loads only
-// the 16-column blocks its tiles touch.  The fragments go to a shared FP32
-// matrix, and the solve, the apply and the residual update are those of
+// the 16-column blocks its tiles touch.  For a whole row the accumulators start
+// from the dense terms alpha0 G_pipi + lambda_r I and R_r.  The fragments go to
+// a shared FP32 matrix, and the solve, the apply and the residual update are those of
 // k_sparse_cta.cuh: blocked Cholesky in 16-column panels with the right-hand
 // side as an extra row, backward substitution, and the residual update from
 // the staged (hi + lo) slices.
@@ -102,6 +103,55 @@ __device__ __forceinline__ void cta_bf_store(const float (&acc)[CtaBfCfg<B>::NPT
     if ((lane & 3) == 0) {
         M[B * SM + 16 * WT::GRAD + r] = gac[0];
         M[B * SM + 16 * WT::GRAD + r + 8] = gac[2];
+    }
+}
+
+// Whole rows: warp W's accumulators start from alpha0 G_pipi + lambda_r I (its
+// tiles) and the gradient accumulator from R_r (column 0 of the E tile).
+template <int B, int W>
+__device__ __forceinline__ void cta_bf_init(float (&acc)[CtaBfCfg<B>::NPT][4], float (&gac)[4], const StepArgs &a,
+                                            int row, float lam, int lane) {
+    using C = CtaBfCfg<B>;
+    using WT = CtaBfWarp<B, W>;
+    const int r = lane >> 2, c2 = 2 * (lane & 3);
+#pragma unroll
+    for (int s = 0; s < C::NPT; ++s) {
+        const int i = WT::ti(s), n = WT::tn(s);
+        const int r0 = 16 * i + r, r1 = r0 + 8, c = 8 * n + c2;
+        const float2 g0 = *reinterpret_cast<const float2 *>(a.G + (int64_t)(a.p0 + r0) * B + c);
+        const float2 g1 = *reinterpret_cast<const float2 *>(a.G + (int64_t)(a.p0 + r1) * B + c);
+        acc[s][0] = a.alpha0 * g0.x + (r0 == c ? lam : 0.f);
+        acc[s][1] = a.alpha0 * g0.y + (r0 == c + 1 ? lam : 0.f);
+        acc[s][2] = a.alpha0 * g1.x + (r1 == c ? lam : 0.f);
+        acc[s][3] = a.alpha0 * g1.y + (r1 == c + 1 ? lam : 0.f);
+    }
+    if ((lane & 3) == 0) {
+        gac[0] = a.R[(int64_t)row * B + 16 * WT::GRAD + r];
+        gac[2] = a.R[(int64_t)row * B + 16 * WT::GRAD + r + 8];
+    }
+}
+
+template <int B>
+__device__ __forceinline__ void cta_bf_init_any(int warp, float (&acc)[CtaBfCfg<B>::NPT][4], float (&gac)[4],
+                                                const StepArgs &a, int row, float lam, int lane) {
+    if constexpr (B == 64) {
+        switch (warp) {
+            case 0: cta_bf_init<B, 0>(acc, gac, a, row, lam, lane); break;
+            case 1: cta_bf_init<B, 1>(acc, gac, a, row, lam, lane); break;
+            case 2: cta_bf_init<B, 2>(acc, gac, a, row, lam, lane); break;
+            default: cta_bf_init<B, 3>(acc, gac, a, row, lam, lane); break;
+        }
+    } else {
+        switch (warp) {
+            case 0: cta_bf_init<B, 0>(acc, gac, a, row, lam, lane); break;
+            case 1: cta_bf_init<B, 1>(acc, gac, a, row, lam, lane); break;
+            case 2: cta_bf_init<B, 2>(acc, gac, a, row, lam, lane); break;
+            case 3: cta_bf_init<B, 3>(acc, gac, a, row, lam, lane); break;
+            case 4: cta_bf_init<B, 4>(acc, gac, a, row, lam, lane); break;
+            case 5: cta_bf_init<B, 5>(acc, gac, a, row, lam, lane); break;
+            case 6: cta_bf_init<B, 6>(acc, gac, a, row, lam, lane); break;
+            default: cta_bf_init<B, 7>(acc, gac, a, row, lam, lane); break;
+        }
     }
 }
 
@@ -196,6 +246,8 @@ __global__ void __launch_bounds__(CtaBfCfg<B>::THREADS, 2) k_sparse_cta_bf16(con
             for (int q = 0; q < 4; ++q) acc[s][q] = 0.f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) gac[q] = 0.f;
+        const float lam = a.lambda * (1.0f + a.nu * (float)tk.len);
+        if (tk.slot < 0) cta_bf_init_any<B>(warp, acc, gac, a, tk.row, lam, lane);
         // chunk j into buffer bi: residual column (hi, lo), zero rows up to the next
         // multiple of 16, and the slices
         auto issue = [&](int j, int bi) {
@@ -243,9 +295,8 @@ __global__ void __launch_bounds__(CtaBfCfg<B>::THREADS, 2) k_sparse_cta_bf16(con
             for (int j = tid; j < B; j += nt) P[B * B + j] = M[B * SM + j];
             continue;
         }
-        const float lam = a.lambda * (1.0f + a.nu * (float)tk.len);
         if (tid == 0) flag[1] = a.force_fp64 ? 1 : 0;
-        cta_dense_terms<B, SM, float>(a, M, diag0, tk.row, lam);
+        for (int i = tid; i < B; i += nt) diag0[i] = M[i * SM + i];  // the dense terms are in already
         __syncthreads();
         cta_chol16<B, SM>(M, invd, diag0, &flag[1], 1e-5f);
         if (flag[1]) {  // CTA-uniform: queue the row for the FP64 re-solve
@@ -258,9 +309,7 @@ __global__ void __launch_bounds__(CtaBfCfg<B>::THREADS, 2) k_sparse_cta_bf16(con
         for (int j = tid; j < B; j += nt) xv[j] = M[B * SM + j];
         __syncthreads();
         cta_backsolve16<B, SM>(M, invd, xv);
-        bool finite = true;
-        for (int j = 0; j < B; ++j) finite = finite && isfinite(xv[j]);
-        if (!finite) {
+        if (!__syncthreads_and(tid >= B || isfinite(xv[tid]))) {
             if (tid == 0) {
                 const int i = atomicAdd(a.retry, 1);
                 a.retry[1 + i] = tk.row;
