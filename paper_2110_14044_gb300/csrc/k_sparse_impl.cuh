@@ -416,11 +416,12 @@ __global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
     const int grp = active ? lane / C::NT : C::NG, t = lane % C::NT;
     const int ti = t >= 6 ? 3 : (t >= 3 ? 2 : (t >= 1 ? 1 : 0));
     const int tj = t - ti * (ti + 1) / 2;
+    int nxt = 0;  // lane 0: the next task index, fetched while the current task runs
+    if (lane == 0) nxt = atomicAdd(a.counter, 1);
     for (;;) {
-        int tsk = 0;
-        if (lane == 0) tsk = atomicAdd(a.counter, 1);
-        tsk = __shfl_sync(kFull, tsk, 0);
+        const int tsk = __shfl_sync(kFull, nxt, 0);
         if (tsk >= a.n_tasks) break;
+        if (lane == 0) nxt = atomicAdd(a.counter, 1);
         const Task tk = a.tasks[tsk];
         const int nch = (tk.len + CH - 1) / CH;
         float acc[T][T], gacc[T];
