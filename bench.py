@@ -37,6 +37,9 @@ WORKLOADS = {
     "ml20m_136k": ("ML20M-shaped synthetic: 136,000 users x 20,000 items, 10,000,000 positives, "
                    "Zipf(1.05) items, lognormal(3.7,1.1) lengths in [5,8000], d=128, b=32, "
                    "alpha0=0.1, lambda=1e-3, nu=1, seed 0"),
+    "skewed_136k": ("ML20M shape with skewed users: 136,000 users x 20,000 items, 10,000,000 "
+                    "positives, Zipf(1.05) items, Zipf(1.3) user activity (rows capped at all "
+                    "20,000 items), d=128, b=32, alpha0=0.1, lambda=1e-3, nu=1, seed 0"),
     "msd_570k": ("MSD-shaped synthetic: 570,000 users x 41,000 items, 34,000,000 positives, "
                  "Zipf(0.9) items, lognormal(3.5,1.2) lengths in [1,41000], d=1024, b=128, "
                  "alpha0=0.02, lambda=2e-3, nu=1, seed 0"),

@@ -9,8 +9,8 @@ interactions, and MSD, 571,355 x 41,140 with 33.6M) are not available here;
 the presets below stand in for them with the same shape:
 
 * item popularity follows a Zipf law over a random permutation of item ids,
-* per-user history lengths are lognormal, clipped, then rescaled so that the
-  total hits |S| exactly,
+* per-user history lengths are lognormal (or Zipf over the users), clipped,
+  then rescaled so that the total hits |S| exactly,
 * within a user row items are drawn without replacement (successive sampling
   from the Zipf weights), so every (u, i) pair occurs at most once,
 * y = alpha = 1 (binary implicit feedback, Section 2: "in most cases
@@ -73,9 +73,15 @@ def _rng(seed: int, stream: int) -> np.random.Generator:
     return np.random.Generator(np.random.Philox(key=[seed, stream]))
 
 
-def _lengths(rng, n_users, nnz, mu, sigma, lo, hi):
-    """Lognormal lengths clipped to [lo, hi], rescaled to sum to nnz exactly."""
-    raw = rng.lognormal(mean=mu, sigma=sigma, size=n_users)
+def _lengths(rng, n_users, nnz, mu, sigma, lo, hi, user_zipf=None):
+    """Lengths clipped to [lo, hi], rescaled to sum to nnz exactly: lognormal(mu,
+    sigma) draws, or (user_zipf = s) Zipf(s) activity over a random permutation of
+    the users (rank r gets weight r^-s)."""
+    if user_zipf is None:
+        raw = rng.lognormal(mean=mu, sigma=sigma, size=n_users)
+    else:
+        raw = np.empty(n_users)
+        raw[rng.permutation(n_users)] = np.arange(1, n_users + 1, dtype=np.float64) ** (-user_zipf)
     if not (lo * n_users <= nnz <= hi * n_users):
         raise ValueError("nnz is not reachable with the given clip range")
 
@@ -181,10 +187,11 @@ def transpose_csr(n_rows, n_cols, indptr, indices):
 
 
 def make_interactions(n_users, n_items, nnz, zipf_s, ln_mu, ln_sigma,
-                      len_min, len_max, seed) -> Interactions:
-    """Draw a binary interaction set with Zipf items and lognormal user lengths."""
+                      len_min, len_max, seed, user_zipf=None) -> Interactions:
+    """Draw a binary interaction set with Zipf items and lognormal (or, with
+    user_zipf, Zipf) user lengths; a row holds at most n_items distinct items."""
     len_max = min(len_max, n_items)
-    lens = _lengths(_rng(seed, 1), n_users, nnz, ln_mu, ln_sigma, len_min, len_max)
+    lens = _lengths(_rng(seed, 1), n_users, nnz, ln_mu, ln_sigma, len_min, len_max, user_zipf)
     rng = _rng(seed, 2)
     p = _zipf_weights(rng, n_items, zipf_s)
     owner, items = _sample_rows(rng, lens, p)
@@ -234,6 +241,12 @@ PRESETS = {
     "ml20m_136k": dict(n_users=136_000, n_items=20_000, nnz=10_000_000, zipf_s=1.05,
                        ln_mu=3.7, ln_sigma=1.1, len_min=5, len_max=8000, d=128, b=32,
                        alpha0=0.1, lam=1e-3, nu=1.0, epochs=16),
+    # ML20M shape with extremely skewed user activity: Zipf(1.3) users; "at most
+    # 200,000 items per row" cannot hold with 20,000 items, so rows are capped at
+    # the whole catalogue.  Swept over d with the block size autotuned.
+    "skewed_136k": dict(n_users=136_000, n_items=20_000, nnz=10_000_000, zipf_s=1.05,
+                        ln_mu=0.0, ln_sigma=0.0, user_zipf=1.3, len_min=5, len_max=200_000,
+                        d=128, b=32, alpha0=0.1, lam=1e-3, nu=1.0, epochs=16),
     # MSD-shaped large workload.
     "msd_570k": dict(n_users=570_000, n_items=41_000, nnz=34_000_000, zipf_s=0.9,
                      ln_mu=3.5, ln_sigma=1.2, len_min=1, len_max=50_000, d=1024, b=128,
@@ -247,7 +260,7 @@ def preset(name: str, seed: int = 0, **overrides) -> Problem:
     cfg.update(overrides)
     data = make_interactions(cfg["n_users"], cfg["n_items"], cfg["nnz"], cfg["zipf_s"],
                              cfg["ln_mu"], cfg["ln_sigma"], cfg["len_min"], cfg["len_max"],
-                             seed)
+                             seed, cfg.get("user_zipf"))
     d = cfg["d"]
     std = 0.1 / math.sqrt(d)
     W0, H0 = init_factors(data.n_users, data.n_items, d, std, seed)

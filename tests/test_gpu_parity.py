@@ -424,3 +424,23 @@ def test_autotuner_returns_the_fastest_admissible_block():
     best16, t16 = autotune.autotune_block_size(prob.data, 64, 0.1, 1e-3, 0.0, epochs=1,
                                                precision=_abi.PREC_BF16, W0=prob.W0, H0=prob.H0)
     assert set(t16) == {16, 32, 64}
+
+
+@pytest.mark.parametrize("b,precision", [(16, _abi.PREC_FP32), (64, _abi.PREC_FP32), (32, _abi.PREC_BF16)])
+def test_skewed_user_activity_epochs(b, precision):
+    """Zipf(1.3) user activity with rows capped at the whole catalogue (the skewed
+    workload's shape, scaled down): every row length class in one launch."""
+    d = 64
+    prob = synth.preset("skewed_136k", seed=9, n_users=3000, n_items=600, nnz=90_000, d=d)
+    data = prob.data
+    assert np.diff(data.u_indptr).max() == data.n_items
+    m = Model(data, d, b, 0.1, 1e-3, 1.0, precision=precision, graph=True, W0=prob.W0, H0=prob.H0)
+    P = oracle.Problem.from_data(data, d, b, 0.1, 1e-3, 1.0)
+    Wr, Hr, _, _, _ = oracle.ialspp(P, 2, prob.W0, prob.H0)
+    ref = oracle.objective(P, Wr, Hr)
+    o, st = m.epoch(2, objective=True)
+    assert st == 0
+    W, H = m.factors()
+    tol_obj, tol_emb = (OBJ_TOL, EMB_TOL) if precision == _abi.PREC_FP32 else (1e-3, 5e-2)
+    assert abs(o - ref) / ref <= tol_obj
+    assert rel_embed_err(W, Wr) <= tol_emb and rel_embed_err(H, Hr) <= tol_emb
