@@ -7,9 +7,10 @@
 // not depend on what it is batched with.  Because H is frozen, the block
 // Hessian A_pi = sum_s h_{s,pi} h_{s,pi}^T + alpha0 G^I_pipi + lambda_u I is the
 // same in every sweep: it is accumulated (8 x 8 thread tiles over its lower
-// triangle, slices staged with cp.async) and factorised (blocked shared-memory
-// Cholesky) once per block, kept in the request's workspace, and reused.  Each
-// sweep then only forms the gradient
+// triangle, slices staged with cp.async) and factorised (Cholesky in 16-column
+// panels) once per block, kept in the request's workspace, and reused.  Each
+// sweep then only forms the gradient (from staged slices; u = w G^I is kept
+// up to date after every apply)
 //   g = alpha0 (w G^I)_pi + lambda_u w_pi + sum_s e_s h_{s,pi}
 // solves L L^T delta = g, applies w_pi -= delta and updates the request's
 // residuals e_s -= <delta, h_{s,pi}> (e starts at -y since w = 0).
@@ -26,37 +27,13 @@ struct FoldCfg {
     static constexpr int NG0 = 256 / NTL;
     static constexpr int NG = NG0 < 8 ? NG0 : 8;
     static constexpr int ACTIVE = NTL * NG;
-    static constexpr int SB = B + 4;
+    static constexpr int SB = B % 32 == 0 ? B + 4 : B + 20;  // = 4 mod 32 (layout of cta_chol16)
     static constexpr int CH = 32;
     static constexpr int BUF = CH * SB;
-    // floats: 2 staging buffers, M (B+1 rows), diag0, invd, x, gradient partials (8 x B), flag
-    static constexpr int FIXED_FLOATS = 2 * BUF + (B + 1) * SB + 3 * B + 8 * B + 4;
+    // floats: 2 staging buffers, staged residuals (2 x CH), M (B+1 rows), diag0, invd, x,
+    // gradient partials (8 x B), flag; then w and u = w G^I (d floats each)
+    static constexpr int FIXED_FLOATS = 2 * BUF + 2 * CH + (B + 1) * SB + 3 * B + 8 * B + 4;
 };
-
-// Forward substitution L z = g (g in x on entry), panel by panel.
-template <int B, int SM>
-__device__ void cta_forwardsolve(const float *M, const float *invd, float *x) {
-    constexpr int NB = B / 8;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int p = 0; p < NB; ++p) {
-        const int k0 = 8 * p;
-        if (tid == 0) {
-            for (int j = 0; j < 8; ++j) {
-                float v = x[k0 + j];
-                for (int m = 0; m < j; ++m) v -= M[(k0 + j) * SM + k0 + m] * x[k0 + m];
-                x[k0 + j] = v * invd[k0 + j];
-            }
-        }
-        __syncthreads();
-        for (int i = k0 + 8 + tid; i < B; i += nt) {
-            float v = x[i];
-#pragma unroll
-            for (int m = 0; m < 8; ++m) v -= M[i * SM + k0 + m] * x[k0 + m];
-            x[i] = v;
-        }
-        __syncthreads();
-    }
-}
 
 template <int B>
 __global__ void __launch_bounds__(256) k_foldin(FoldArgs a) {
@@ -65,13 +42,15 @@ __global__ void __launch_bounds__(256) k_foldin(FoldArgs a) {
     extern __shared__ float4 smem4[];
     float *smem = reinterpret_cast<float *>(smem4);
     float *buf0 = smem;
-    float *M = buf0 + 2 * C::BUF;
+    float *she = buf0 + 2 * C::BUF;     // residuals of the staged chunks [2][CH]
+    float *M = she + 2 * CH;
     float *diag0 = M + (B + 1) * SB;
     float *invd = diag0 + B;
     float *xv = invd + B;
     float *gp = xv + B;                 // 8 x B gradient partials
     int *flag = reinterpret_cast<int *>(gp + 8 * B);
-    float *wv = reinterpret_cast<float *>(flag + 4);  // d floats
+    float *wv = reinterpret_cast<float *>(flag + 4);  // w (d floats)
+    float *uv = wv + a.d;                              // u = w G^I (d floats)
     const int tid = threadIdx.x, nt = blockDim.x;
     const int d = a.d, nb = d / B;
     const bool active = tid < C::ACTIVE;
@@ -90,7 +69,7 @@ __global__ void __launch_bounds__(256) k_foldin(FoldArgs a) {
         float *wout = reinterpret_cast<float *>(base + rq.w_off);
         const float lam = a.lambda * (1.0f + a.nu * (float)n);
         for (int s = tid; s < n; s += nt) ev[s] = rq.has_y ? -yv[s] : -1.0f;
-        for (int j = tid; j < d; j += nt) wv[j] = 0.f;
+        for (int j = tid; j < d; j += nt) wv[j] = uv[j] = 0.f;
         if (tid == 0) flag[1] = 0;
         __syncthreads();
         // ---- per block: Hessian, factor, keep
@@ -153,51 +132,83 @@ __global__ void __launch_bounds__(256) k_foldin(FoldArgs a) {
             }
             for (int j = tid; j < B; j += nt) M[B * SB + j] = 0.f;
             __syncthreads();
-            cta_cholesky<B, SB, float>(M, invd, diag0, &flag[1], 1e-5f);
+            cta_chol16<B, SB>(M, invd, diag0, &flag[1], 1e-5f);
             float *Lk = Lg + (int64_t)k * (B * B + B);
             for (int e = tid; e < B * B; e += nt) Lk[e] = M[(e / B) * SB + (e % B)];
             for (int j = tid; j < B; j += nt) Lk[B * B + j] = invd[j];
             __syncthreads();
         }
-        // ---- sweeps of gradient, solve, apply, residual update
+        // ---- sweeps of gradient, solve, apply, residual update.  The request's
+        // slices of block k are staged chunk by chunk (cp.async, two buffers) for
+        // the gradient pass and again for the residual pass; u = w G^I is kept up
+        // to date after every apply, so the alpha0 (w G^I)_pi term is a lookup.
+        const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+        const int gsz = nt / B < 8 ? nt / B : 8;  // gradient groups (gp holds 8 partial rows)
+        const int gj = tid % B, gg = tid / B;
+        const int nch = (n + CH - 1) / CH;
+        auto stage = [&](int ch, int p0, int bi, bool with_e) {
+            const int cnt = min(CH, n - ch * CH);
+            float *bufp = buf0 + bi * C::BUF;
+            for (int f = tid; f < cnt * (B / 4); f += nt) {
+                const int kk = f / (B / 4), v = f % (B / 4);
+                const int64_t item = items[ch * CH + kk];
+                cp_async16(bufp + kk * SB + 4 * v, a.H + item * d + p0 + 4 * v);
+            }
+            if (with_e && tid < cnt) she[bi * CH + tid] = ev[ch * CH + tid];
+            cp_async_commit();
+        };
         for (int sw = 0; sw < a.sweeps && !flag[1]; ++sw) {
             for (int k = 0; k < nb; ++k) {
                 const int p0 = k * B;
-                // gradient: thread (g, j) with j < B, g < nt / B sums a strided share
-                const int gsz = nt / B < 8 ? nt / B : 8;  // gp holds 8 partial rows
-                const int j = tid % B, g = tid / B;
-                if (g < gsz) {
-                    float t = 0.f;
-                    for (int s = g; s < n; s += gsz) t += ev[s] * a.H[(int64_t)items[s] * d + p0 + j];
-                    if (g == 0) {
-                        float u = 0.f;
-                        for (int q = 0; q < d; ++q) u += wv[q] * a.G[(int64_t)q * d + p0 + j];
-                        t += a.alpha0 * u + lam * wv[p0 + j];
-                    }
-                    gp[g * B + j] = t;
+                float t = 0.f;
+                if (nch > 0) stage(0, p0, 0, true);
+                for (int ch = 0; ch < nch; ++ch) {
+                    const int bi = ch & 1;
+                    cp_async_wait_all();
+                    __syncthreads();
+                    if (ch + 1 < nch) stage(ch + 1, p0, bi ^ 1, true);
+                    const int cnt = min(CH, n - ch * CH);
+                    const float *bp = buf0 + bi * C::BUF;
+                    if (gg < gsz)
+                        for (int kk = gg; kk < cnt; kk += gsz) t += she[bi * CH + kk] * bp[kk * SB + gj];
                 }
+                if (gg < gsz) gp[gg * B + gj] = t;
                 const float *Lk = Lg + (int64_t)k * (B * B + B);
                 for (int e = tid; e < B * B; e += nt) M[(e / B) * SB + (e % B)] = Lk[e];
                 for (int q = tid; q < B; q += nt) invd[q] = Lk[B * B + q];
                 __syncthreads();
                 for (int q = tid; q < B; q += nt) {
-                    float t = 0.f;
-                    for (int gg = 0; gg < gsz; ++gg) t += gp[gg * B + q];
-                    xv[q] = t;
+                    float v = a.alpha0 * uv[p0 + q] + lam * wv[p0 + q];
+                    for (int g2 = 0; g2 < gsz; ++g2) v += gp[g2 * B + q];
+                    xv[q] = v;
                 }
                 __syncthreads();
-                cta_forwardsolve<B, SB>(M, invd, xv);
-                cta_backsolve<B, SB, float>(M, invd, xv);
+                cta_forward16<B, SB>(M, invd, xv);
+                cta_backsolve16<B, SB>(M, invd, xv);
+                // apply, then u -= delta^T G^I[pi, :] (coalesced over the columns of G^I)
                 for (int q = tid; q < B; q += nt) wv[p0 + q] -= xv[q];
-                // residuals: one warp per interaction, lanes split the block
-                const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-                for (int s = warp; s < n; s += nw) {
-                    const float *h = a.H + (int64_t)items[s] * d + p0;
-                    float t = 0.f;
-                    for (int q = lane; q < B; q += 32) t += xv[q] * h[q];
+                for (int q = tid; q < d; q += nt) {
+                    float v = 0.f;
+#pragma unroll 8
+                    for (int m = 0; m < B; ++m) v += xv[m] * a.G[(int64_t)(p0 + m) * d + q];
+                    uv[q] -= v;
+                }
+                // residuals e_s -= <delta, h_{s,pi}>: one warp per staged interaction
+                if (nch > 0) stage(0, p0, 0, false);
+                for (int ch = 0; ch < nch; ++ch) {
+                    const int bi = ch & 1;
+                    cp_async_wait_all();
+                    __syncthreads();
+                    if (ch + 1 < nch) stage(ch + 1, p0, bi ^ 1, false);
+                    const int cnt = min(CH, n - ch * CH);
+                    const float *bp = buf0 + bi * C::BUF;
+                    for (int kk = warp; kk < cnt; kk += nw) {
+                        float v = 0.f;
+                        for (int q = lane; q < B; q += 32) v += xv[q] * bp[kk * SB + q];
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
-                    if (lane == 0) ev[s] -= t;
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+                        if (lane == 0) ev[ch * CH + kk] -= v;
+                    }
                 }
                 __syncthreads();
             }
@@ -210,7 +221,7 @@ __global__ void __launch_bounds__(256) k_foldin(FoldArgs a) {
 
 template <int B>
 int foldin_smem(int d) {
-    return (FoldCfg<B>::FIXED_FLOATS + d) * 4 + 16;
+    return (FoldCfg<B>::FIXED_FLOATS + 2 * d) * 4 + 16;
 }
 
 template <int B>

@@ -268,6 +268,41 @@ __device__ void cta_chol16(float *M, float *invd, const float *diag0, int *bad, 
     }
 }
 
+// Forward substitution L z = g for a factor left by cta_chol16 (g in x on entry),
+// 16-blocks from the top: warp 0 solves the block with shuffles, then all
+// threads remove its contribution from the entries below it.
+template <int B, int SM>
+__device__ void cta_forward16(const float *M, const float *invd, float *x) {
+    constexpr int P = 16, NP = B / P;
+    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
+#pragma unroll 1
+    for (int p = 0; p < NP; ++p) {
+        const int k0 = P * p;
+        if (warp == 0) {
+            const int m = lane & (P - 1);
+            float z = x[k0 + m];
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                const float zj = __shfl_sync(kFull, z * invd[k0 + j], j);
+                if (m > j) z -= M[(k0 + m) * SM + k0 + j] * zj;
+                else if (m == j) z = zj;
+            }
+            if (lane < P) x[k0 + m] = z;
+        }
+        __syncthreads();
+        for (int q = k0 + P + tid; q < B; q += nt) {
+            float v = x[q];
+#pragma unroll
+            for (int j = 0; j < P; j += 4) {
+                const float4 l = *reinterpret_cast<const float4 *>(M + q * SM + k0 + j);
+                v -= l.x * x[k0 + j] + l.y * x[k0 + j + 1] + l.z * x[k0 + j + 2] + l.w * x[k0 + j + 3];
+            }
+            x[q] = v;
+        }
+        __syncthreads();
+    }
+}
+
 // Backward substitution L^T x = z for the factor left by cta_chol16 (z in x on
 // entry), 16-blocks from the bottom: warp 0 solves the block with shuffles, then
 // all threads remove its contribution from the entries above it.
