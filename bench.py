@@ -53,9 +53,9 @@ METRIC = "iALS++ epoch throughput (row-block solves/s = (|U|+|I|)*d/b per epoch)
 NCU_TRAFFIC = {
     ("sparse", "bf16"): {"sources": ["paper_2110_14044_gb300/csrc/k_sparse_bf16.cuh",
                                      "paper_2110_14044_gb300/csrc/k_sparse_impl.cuh"],
-                         "sha256_16": "da96ecf5aec807a1", "bytes_per_launch": 289.2e6},
+                         "sha256_16": "92e53fea777e2073", "bytes_per_launch": 289.3e6},
     ("sparse", "fp32"): {"sources": ["paper_2110_14044_gb300/csrc/k_sparse_impl.cuh"],
-                         "sha256_16": "8371fb2a2c60dbb9", "bytes_per_launch": 188.7e6},
+                         "sha256_16": "4034457432923fba", "bytes_per_launch": 183.7e6},
 }
 
 
@@ -430,6 +430,25 @@ def run_ncu_step(args):
     print("ncu-step done")
 
 
+def run_ncu_foldin(n_req=16, seed=0):
+    """A few fold-in requests of the serving workload (for profiler captures)."""
+    import paper_2110_14044_gb300 as ials
+    from paper_2110_14044_gb300 import build
+    build.build()
+    rng = np.random.Generator(np.random.Philox(key=[seed, 7]))
+    n_items, d = 41000, 256
+    H = rng.normal(0.0, 0.05, (n_items, d)).astype(np.float32)
+    srv = ials.FoldinServer(H, d, 64, 0.1, 1e-3, 1.0, sweeps=4, workspace_bytes=1 << 30)
+    tickets = []
+    for _ in range(n_req):
+        n = int(np.exp(rng.uniform(0.0, np.log(5000.0))))
+        tickets.append(srv.submit(rng.choice(n_items, n, replace=False).astype(np.int32)))
+    for t in tickets:
+        srv.result(t)
+    srv.close()
+    print("ncu-foldin done")
+
+
 # ----------------------------------------------------------------- fold-in serving
 FOLDIN_DESC = ("fold-in: frozen H 41,000 x 256 ~ N(0, 0.05^2), b=64, 4 sweeps, alpha0=0.1, "
                "lambda=1e-3, nu=1; open loop: Poisson arrivals at each rate; closed loop: C "
@@ -591,9 +610,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-step", action="store_true",
                     help="run one user and one item block step only (for profiler captures)")
+    ap.add_argument("--ncu-foldin", action="store_true",
+                    help="serve a few fold-in requests only (for profiler captures)")
     args = ap.parse_args()
     if args.ncu_step:
         run_ncu_step(args)
+    elif args.ncu_foldin:
+        run_ncu_foldin()
     elif args.impl == "reference":
         run_reference(args)
     else:
