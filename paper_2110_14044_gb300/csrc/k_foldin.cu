@@ -28,7 +28,7 @@ struct FoldCfg {
     static constexpr int NG = NG0 < 8 ? NG0 : 8;
     static constexpr int ACTIVE = NTL * NG;
     static constexpr int SB = B % 32 == 0 ? B + 4 : B + 20;  // = 4 mod 32 (layout of cta_chol16)
-    static constexpr int CH = 32;
+    static constexpr int CH = B <= 64 ? 128 : 64;  // interactions staged per chunk
     static constexpr int BUF = CH * SB;
     // floats: 2 staging buffers, staged residuals (2 x CH), M (B+1 rows), diag0, invd, x,
     // gradient partials (8 x B), flag; then w and u = w G^I (d floats each)
