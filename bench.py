@@ -247,7 +247,10 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local_rank)
     from paper_2110_14044_gb300 import _abi, build, synth
-    build.build()
+    if rank == 0:
+        build.build()   # one rank builds (a no-op when the library is up to date) ...
+    if world > 1:
+        torch.distributed.barrier()  # ... before any rank loads it
     import paper_2110_14044_gb300 as ials
 
     prob = synth.preset(args.workload, seed=0, **overrides(args))
