@@ -14,7 +14,8 @@
 // applied) and are gathered with cp.async into two staging buffers.  One
 // ldmatrix.x4.trans of a 16 x 16 block serves both as the A fragment of an
 // m-tile and as the B fragments of the two matching n-tiles.  The Newton solve
-// (warp Gauss-Jordan, FP32) and the apply are those of the FP32 kernels.  The
+// is the warp Gauss-Jordan elimination with 2 x 2 pivot blocks (FP32), the
+// apply that of the FP32 kernels.  The
 // residual update e_s -= <delta, f_s> is again a tensor-core product: the
 // staged tile times delta (split hi + lo, compensated the same way) as the
 // only non-zero column of an m16n8k16 B operand.
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
         for (int j = 0; j < B; ++j) A[j] += sGpp[j * B + col] + (j == col ? lam : 0.f);
         g += a.R[(int64_t)row * B + col];
         float delta;
-        if (!chol_solve<B>(A, g, col, sub, w, a.force_fp64 != 0, delta)) {
+        if (!gj_solve2<B>(A, g, col, sub, w, a.force_fp64 != 0, delta)) {
             queue_retry(a, lane, row);
             continue;
         }

@@ -34,7 +34,7 @@ struct SparseCfg {
     static constexpr int CH = 32;                  // interactions staged per chunk
     static constexpr int VPAD = (B + 3) / 4 * 4;
     static constexpr int CB = B % 4 == 0 ? B + 4 : B + 1;  // solver column buffer (B entries + g_k)
-    static constexpr int LREG = 2 * CB;                     // two column buffers
+    static constexpr int LREG = 4 * CB;                     // two steps x two column buffers
     static constexpr int WARP_FLOATS_RAW = CH * SB + 3 * CH + VPAD + LREG;
     static constexpr int WARP_FLOATS = (WARP_FLOATS_RAW + 3) / 4 * 4;
     static constexpr int GPP_FLOATS = (B * B + 3) / 4 * 4;
@@ -144,6 +144,73 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // no more than ~17 bits lost); one vote at the end decides for the warp.
 // Returns false (warp-uniform) on a bad pivot or a non-finite solution; on
 // success `delta` holds entry col of the solution.
+// Gauss-Jordan as above with 2 x 2 pivot blocks (B even): step m eliminates the
+// columns k = 2m and k + 1 at once.  Lanes publish both column entries (lanes k
+// and k + 1 also g_k, g_{k+1}); the pivot block P = [[a, b], [b, c]] is SPD (a
+// principal Schur complement), and every other lane eliminates with
+//   [s1, s2] = [A[col][k], A[col][k+1]] P^{-1},
+//   A[col][j] -= s1 A[k][j] + s2 A[k+1][j] (j > k + 1),  g_col -= s1 g_k + s2 g_{k+1}.
+// At the end the system is block diagonal; each pivot pair solves its 2 x 2
+// block (the partner's g by a shuffle).  The pivots checked are those of
+// A = L D L^T: d_k = a and d_{k+1} = c - b^2 / a.  Half as many dependent steps
+// as the scalar version for the same multiply-adds.
+template <int B>
+__device__ __forceinline__ bool gj_solve2(float (&A)[B], float g, int col, int sub, const WarpSmem &w,
+                                          bool force_fail, float &delta) {
+    static_assert(B % 4 == 0, "pairs of columns, 16-byte loads");
+    constexpr int CB = SparseCfg<B>::CB;
+    float diag0 = 0.f;
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+        if (j == col) diag0 = A[j];
+    bool bad = force_fail;
+    float pa = 1.f, pb = 0.f, pc = 1.f;  // this lane's pivot block
+#pragma unroll
+    for (int k = 0; k < B; k += 2) {
+        float *v1 = w.L + ((k >> 1) & 1) * 2 * CB, *v2 = v1 + CB;
+        if (sub == 0) {
+            v1[col] = A[k];
+            v2[col] = A[k + 1];
+            if (col == k) v1[B] = g;
+            if (col == k + 1) v2[B] = g;
+        }
+        __syncwarp();
+        const float a = v1[k], b = v1[k + 1], c = v2[k + 1];
+        const float g1 = v1[B], g2 = v2[B];
+        const float rdet = rcp_approx(a * c - b * b);
+        const bool piv = col == k || col == k + 1;
+        const float x = A[k], y = A[k + 1];
+        const float s1 = piv ? 0.f : (x * c - y * b) * rdet;
+        const float s2 = piv ? 0.f : (y * a - x * b) * rdet;
+        if (col == k) bad = bad || !(a > 1e-5f * diag0) || !(a <= 3.0e38f);
+        if (col == k + 1) {
+            const float d1 = c - b * b * rcp_approx(a);
+            bad = bad || !(d1 > 1e-5f * diag0) || !(d1 <= 3.0e38f);
+        }
+        if (piv) {
+            pa = a;
+            pb = b;
+            pc = c;
+        }
+#pragma unroll
+        for (int j0 = (k + 2) & ~3; j0 < B; j0 += 4) {
+            const float4 q1 = *reinterpret_cast<const float4 *>(v1 + j0);
+            const float4 q2 = *reinterpret_cast<const float4 *>(v2 + j0);
+            if (j0 > k + 1) A[j0] -= s1 * q1.x + s2 * q2.x;
+            if (j0 + 1 > k + 1) A[j0 + 1] -= s1 * q1.y + s2 * q2.y;
+            if (j0 + 2 > k + 1) A[j0 + 2] -= s1 * q1.z + s2 * q2.z;
+            A[j0 + 3] -= s1 * q1.w + s2 * q2.w;
+        }
+        g -= s1 * g1 + s2 * g2;
+    }
+    if (__any_sync(kFull, bad)) return false;
+    // 2 x 2 block solve: lane col pairs with col ^ 1 (same sub-group lanes)
+    const float gp = __shfl_xor_sync(kFull, g, 1);
+    const float rd = rcp_approx(pa * pc - pb * pb);
+    delta = (col & 1) ? (pa * g - pb * gp) * rd : (pc * g - pb * gp) * rd;
+    return __all_sync(kFull, isfinite(delta));
+}
+
 template <int B>
 __device__ __forceinline__ bool chol_solve(float (&A)[B], float g, int col, int sub,
                                            const WarpSmem &w, bool force_fail, float &delta) {
