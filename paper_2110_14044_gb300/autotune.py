@@ -3,7 +3,8 @@
 The block size b of iALS++ changes the work per epoch (the sparse statistics
 grow with b^2 per interaction, the solves with b^3 per row, the number of
 passes over S with d / b) but not the quality of the model (Section 5.2.2, Fig.
-2: final quality is flat in b).  It is therefore a system parameter: this
+2: final quality is flat in b).  The candidates run from b = 1 (iCD, Alg. 2)
+to b = d (iALS, Alg. 1) where d allows.  It is therefore a system parameter: this
 module times one epoch of the library for every admissible b on the given
 workload and returns the fastest, together with the measured table.
 
@@ -16,7 +17,7 @@ import numpy as np
 
 from . import _abi
 
-CANDIDATES = (8, 16, 32, 64, 128)
+CANDIDATES = (1, 2, 4, 8, 16, 32, 64, 128)  # b = 1 is iCD (Alg. 2); b = d is iALS (Alg. 1)
 
 
 def admissible(d: int, b: int, precision: int) -> bool:

@@ -419,7 +419,7 @@ def test_autotuner_returns_the_fastest_admissible_block():
     prob = small(d=64, seed=60)
     best, table = autotune.autotune_block_size(prob.data, 64, 0.1, 1e-3, 0.0, epochs=1,
                                                W0=prob.W0, H0=prob.H0)
-    assert set(table) == {8, 16, 32, 64}
+    assert set(table) == {1, 2, 4, 8, 16, 32, 64}
     assert best == min(table, key=table.get) and all(v > 0 for v in table.values())
     best16, t16 = autotune.autotune_block_size(prob.data, 64, 0.1, 1e-3, 0.0, epochs=1,
                                                precision=_abi.PREC_BF16, W0=prob.W0, H0=prob.H0)
@@ -444,3 +444,30 @@ def test_skewed_user_activity_epochs(b, precision):
     tol_obj, tol_emb = (OBJ_TOL, EMB_TOL) if precision == _abi.PREC_FP32 else (1e-3, 5e-2)
     assert abs(o - ref) / ref <= tol_obj
     assert rel_embed_err(W, Wr) <= tol_emb and rel_embed_err(H, Hr) <= tol_emb
+
+
+def test_profile_and_work_model_hooks():
+    """bench.py's measurement hooks: per-kernel event times cover the profiled epochs,
+    launch counts follow the block structure, and with no split rows the sparse step's
+    algorithmic bytes are the per-interaction figure (column id, b-slice, residual read
+    and write, plus the position map on the item side) and the per-row terms."""
+    n_users, n_items, d, b = 400, 300, 32, 8
+    rng = np.random.default_rng(71)
+    u, i = np.nonzero(rng.random((n_users, n_items)) < 0.05)   # short rows only: no splits
+    data = synth.from_pairs(n_users, n_items, u, i)
+    W0, H0 = synth.init_factors(n_users, n_items, d, 0.1 / np.sqrt(d), 71)
+    m = Model(data, d, b, 0.1, 1e-3, 0.5, W0=W0, H0=H0)
+    epochs, nb = 2, d // b
+    kern, total, st = _abi.ials_profile_epochs(m.ctx, epochs)
+    assert st == 0 and total > 0
+    ms = sum(v[0] for v in kern.values())
+    assert 0.3 * total <= ms <= 1.05 * total
+    assert kern["residual"][1] == epochs
+    assert kern["sparse"][1] == epochs * nb * 2
+    assert kern["split_solve"][1] == 0 and kern["split_resid"][1] == 0
+    work = _abi.ials_work_model(m.ctx)
+    nnz, rows = data.nnz, n_users + n_items
+    per_nz = (4 + 4 * b + 4 + 4) + (4 + 4 * b + 4 + 4 + 4)      # user side + item side
+    per_row = 4 * b + 8 * b + 16 + 24                           # R read, x read/write, ptr, task
+    assert work["sparse"][0] == pytest.approx(nb * (nnz * per_nz + rows * per_row), rel=1e-12)
+    assert work["sparse"][1] > 0 and work["gram"][1] == pytest.approx(nb * 2 * 2 * rows * 0 + nb * 2 * (n_items + n_users) * d * b)
