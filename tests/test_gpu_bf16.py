@@ -166,3 +166,31 @@ def test_tcgen05_gramian(n, d, p0, bs):
     got = G.cpu().numpy()
     err = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-30)
     assert err <= 1e-4, err
+
+
+def test_msd_shaped_subsample_bf16_b128_sampled_rows():
+    """The d = 1024 configuration (BF16 pattern, b = 128) on its 1% user subsample
+    (5,700 users x 41,000 items, 340,000 positives; a whole oracle epoch there takes
+    minutes of FP64 Cholesky): after one GPU epoch, one user and one item block step
+    are checked row by row against the oracle evaluated from the same state, on the
+    longest rows and a random sample."""
+    prob = synth.preset("msd_570k", seed=0, n_users=5700, nnz=340_000)
+    assert prob.d == 1024 and prob.b == 128
+    data = prob.data
+    m = Model(data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu, W0=prob.W0, H0=prob.H0)
+    assert m.epoch(1)[1] == 0
+    P = oracle.Problem.from_data(data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu)
+    rng = np.random.default_rng(3)
+    for side, block in ((0, 2), (1, 2)):
+        W, H = m.factors()
+        yhat = m.residuals().astype(np.float64) + 1.0
+        lens = np.diff(data.u_indptr if side == 0 else data.i_indptr)
+        rows = np.unique(np.concatenate([np.argsort(-lens)[:4], rng.integers(0, lens.size, 40)]))
+        st, ref = oracle.rows_step(P, side, block, W, H, yhat, rows)
+        assert np.all(st == 0)
+        assert m.block_step(side, block) == 0
+        W2, H2 = m.factors()
+        got = (W2 if side == 0 else H2)[rows, block * prob.b:(block + 1) * prob.b]
+        err = np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-12)
+        print(f"side {side}: max row rel err {err.max():.2e}")
+        assert err.max() <= 1e-3, (side, err.max())
