@@ -308,6 +308,20 @@ def run_ours(args):
                 "peak_source": peak_src,
                 "bytes_per_launch": dbytes / max(dcnt, 1), "ms_per_launch": dms / max(dcnt, 1),
                 "gflops": work[dom][1] * args.steps / (dms / 1e3) / 1e9}
+    # every kernel kind against its own roofline: algorithmic bytes / event time against the
+    # measured copy bandwidth; FLOPs against the tensor peak (BF16 tensor-core kernels: the
+    # measured burst bf16 peak) or the FP32 FMA peak (152 SMs x 128 FMA x 2 x max SM clock)
+    fma_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    tensor_kinds = ("gram", "rowterm", "sparse") if prec == _abi.PREC_BF16 else ()
+    per_kind = {}
+    for k, (kms, kcnt) in kern.items():
+        if kms <= 0 or k == "objective":
+            continue
+        gbs = work[k][0] * args.steps / (kms / 1e3) / 1e9
+        tfs = work[k][1] * args.steps / (kms / 1e3) / 1e12
+        fpk = peaks.get("bf16_tflops", 1900.0) if k in tensor_kinds else fma_peak
+        per_kind[k] = {"ms_per_epoch": kms / args.steps, "GB/s": gbs, "hbm_frac": gbs / hbm_peak,
+                       "TFLOP/s": tfs, "flop_peak": fpk, "flop_frac": tfs / fpk}
 
     # end to end through the public API: factors in from pinned host memory,
     # one epoch, factors back to pinned host memory, every step
@@ -344,6 +358,7 @@ def run_ours(args):
         "kernels_ms_per_epoch": {k: v[0] / args.steps for k, v in kern.items()},
         "profiled_epoch_ms": prof_total / args.steps,
         "roofline": roofline,
+        "kernels_roofline": per_kind,
         "e2e": {"value": job_throughput(rows_per_epoch, world, e2e_ms), "unit": "rows/s",
                 "h2d_bytes_per_step": fb, "d2h_bytes_per_step": fb, "ms_per_step": e2e_ms},
         "gpu_launches": int(round(launches_per_epoch * args.steps)),
