@@ -48,13 +48,16 @@ WORKLOAD_DESC = WORKLOADS[WORKLOAD]
 METRIC = "iALS++ epoch throughput (row-block solves/s = (|U|+|I|)*d/b per epoch)"
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from the ncu capture
-# summarised under profiles/ (per precision); valid only for the kernel sources it
-# was taken on (sha256 of the listed files, concatenated, first 16 hex digits).
+# summarised under profiles/ (per precision); valid only for the workload (name, d, b)
+# and the kernel sources it was taken on (sha256 of the listed files, concatenated,
+# first 16 hex digits).
 NCU_TRAFFIC = {
-    ("sparse", "bf16"): {"sources": ["paper_2110_14044_gb300/csrc/k_sparse_bf16.cuh",
+    ("sparse", "bf16"): {"workload": ("ml20m_136k", 128, 32),
+                         "sources": ["paper_2110_14044_gb300/csrc/k_sparse_bf16.cuh",
                                      "paper_2110_14044_gb300/csrc/k_sparse_impl.cuh"],
                          "sha256_16": "505b410a0222cb19", "bytes_per_launch": 278.2e6},
-    ("sparse", "fp32"): {"sources": ["paper_2110_14044_gb300/csrc/k_sparse_impl.cuh"],
+    ("sparse", "fp32"): {"workload": ("ml20m_136k", 128, 32),
+                         "sources": ["paper_2110_14044_gb300/csrc/k_sparse_impl.cuh"],
                          "sha256_16": "2ee5d5838c1b6433", "bytes_per_launch": 181.5e6},
 }
 
@@ -67,9 +70,13 @@ def sources_hash(paths):
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kind, precision):
+def measured_traffic(kind, precision, workload=None):
+    """The recorded DRAM bytes per launch, if they were taken on this workload (name, d, b)
+    and on the kernel sources as they are now; else None."""
     rec = NCU_TRAFFIC.get((kind, precision))
     if not rec or not rec["bytes_per_launch"]:
+        return None
+    if workload is not None and tuple(workload) != tuple(rec["workload"]):
         return None
     try:
         h = sources_hash(rec["sources"])
@@ -304,7 +311,7 @@ def run_ours(args):
     dbytes = work[dom][0] * args.steps  # bytes over all profiled launches
     achieved = dbytes / (dms / 1e3) / 1e9
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": measured_traffic(dom, args.precision),
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": measured_traffic(dom, args.precision, (args.workload, prob.d, prob.b)),
                 "peak_source": peak_src,
                 "bytes_per_launch": dbytes / max(dcnt, 1), "ms_per_launch": dms / max(dcnt, 1),
                 "gflops": work[dom][1] * args.steps / (dms / 1e3) / 1e9}
