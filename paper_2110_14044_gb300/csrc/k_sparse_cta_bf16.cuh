@@ -394,7 +394,7 @@ cudaError_t launch_sparse_cta_bf16_all(const StepArgs &a, cudaStream_t s) {
         prof_mark(a.prof, -1, s);
     }
     {  // always called: the first call sizes the grid, outside any stream capture
-        const cudaError_t e = launch_split_resid_reg<B, PERM>(a, s);
+        const cudaError_t e = launch_split_resid_reg_bf16<B, PERM>(a, s);
         if (e != cudaSuccess) return e;
     }
     prof_mark(a.prof, K_RETRY, s);

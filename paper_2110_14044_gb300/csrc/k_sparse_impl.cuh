@@ -819,6 +819,121 @@ __global__ void __launch_bounds__(256) k_split_resid_reg(const StepArgs a) {
     }
 }
 
+// The same residual update for the BF16 path, gathering the fixed side's hi and
+// lo shadows (the arrays the BF16 sparse kernel reads) instead of the FP32
+// factors, so the item pass keeps one copy of the fixed side hot in L2;
+// f = hi + lo is formed in FP32, as in the BF16 kernel's own residual update.
+// SG lanes share an interaction, one 16-byte chunk (8 coordinates) of hi and of
+// lo each, with U interactions per sub-group loaded before any is reduced.
+template <int B>
+struct ResRegBfCfg {
+    static constexpr int NV8 = B / 8;                    // 16-byte chunks per slice
+    static constexpr int SG = NV8 < 8 ? NV8 : 8;         // lanes per interaction
+    static constexpr int SGL = SG == 1 ? 0 : SG == 2 ? 1 : SG == 4 ? 2 : 3;
+    static constexpr int NSUB = 32 / SG, MAXV = NV8 / SG;
+    static constexpr int U = SG < 4 ? SG : 4;
+};
+
+template <int B, bool PERM>
+__global__ void __launch_bounds__(256) k_split_resid_reg_bf16(const StepArgs a) {
+    using C = ResRegBfCfg<B>;
+    constexpr int SGL = C::SGL, SG = C::SG, NSUB = C::NSUB, MAXV = C::MAXV, U = C::U, NV8 = C::NV8;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane >> SGL, sl = lane & (SG - 1);
+    const uint4 *Fh = reinterpret_cast<const uint4 *>(a.Fh);
+    const uint4 *Fl = reinterpret_cast<const uint4 *>(a.Fl);
+    const int64_t d8 = a.d >> 3, p8 = a.p0 >> 3;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(a.counter, 1);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= a.n_stasks) break;
+        const Task tk = a.stasks[t];
+        float dv[MAXV][8];
+#pragma unroll
+        for (int m = 0; m < MAXV; ++m)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dv[m][q] = a.delta[(int64_t)tk.srow * B + 8 * (sl + m * SG) + q];
+        const int64_t beg = tk.begin, end = tk.begin + tk.len;
+        int my_c = 0, my_q = 0;
+        if (beg + lane < end) {
+            my_c = a.idx[beg + lane];
+            my_q = PERM ? a.pos[beg + lane] : (int)(beg + lane);
+        }
+        for (int64_t s0 = beg; s0 < end; s0 += 32) {
+            const int cnt = (int)min((int64_t)32, end - s0);
+            int nx_c = 0, nx_q = 0;
+            if (s0 + 32 + lane < end) {
+                nx_c = a.idx[s0 + 32 + lane];
+                nx_q = PERM ? a.pos[s0 + 32 + lane] : (int)(s0 + 32 + lane);
+            }
+#pragma unroll
+            for (int m0 = 0; m0 < SG; m0 += U) {
+                float acc[U];
+                uint4 hv[U][MAXV], lv[U][MAXV];
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    const int k = sub + NSUB * (m0 + q);
+                    const int64_t c = __shfl_sync(kFull, my_c, k);
+                    acc[q] = 0.f;
+#pragma unroll
+                    for (int m = 0; m < MAXV; ++m) {
+                        const int v = sl + m * SG;
+                        const bool ok = k < cnt && v < NV8;
+                        hv[q][m] = ok ? __ldg(Fh + c * d8 + p8 + v) : make_uint4(0u, 0u, 0u, 0u);
+                        lv[q][m] = ok ? __ldg(Fl + c * d8 + p8 + v) : make_uint4(0u, 0u, 0u, 0u);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+#pragma unroll
+                    for (int m = 0; m < MAXV; ++m) {
+                        const unsigned hw[4] = {hv[q][m].x, hv[q][m].y, hv[q][m].z, hv[q][m].w};
+                        const unsigned lw[4] = {lv[q][m].x, lv[q][m].y, lv[q][m].z, lv[q][m].w};
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const float2 fh = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hw[r]));
+                            const float2 fl = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&lw[r]));
+                            acc[q] += dv[m][2 * r] * (fh.x + fl.x) + dv[m][2 * r + 1] * (fh.y + fl.y);
+                        }
+                    }
+#pragma unroll
+                    for (int o = SG >> 1; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(kFull, acc[q], o);
+                }
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    const int k = sub + NSUB * (m0 + q);
+                    const int qk = __shfl_sync(kFull, my_q, k);
+                    if (sl == 0 && k < cnt) a.e[qk] -= acc[q];
+                }
+            }
+            my_c = nx_c;
+            my_q = nx_q;
+        }
+    }
+}
+
+template <int B, bool PERM>
+cudaError_t launch_split_resid_reg_bf16(const StepArgs &a, cudaStream_t s) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int n = 0;
+        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_split_resid_reg_bf16<B, PERM>, 256, 0);
+        if (err != cudaSuccess) return err;
+        per_sm = n > 0 ? n : 1;
+    }
+    if (a.n_stasks <= 0) return cudaSuccess;
+    cudaError_t err = cudaMemsetAsync(a.counter, 0, sizeof(int32_t), s);
+    if (err != cudaSuccess) return err;
+    int grid = 152 * per_sm;
+    const int need = (a.n_stasks + 7) / 8;
+    if (grid > need) grid = need;
+    prof_mark(a.prof, K_SPLIT_RESID, s);
+    k_split_resid_reg_bf16<B, PERM><<<grid, 256, 0, s>>>(a);
+    prof_mark(a.prof, -1, s);
+    return cudaGetLastError();
+}
+
 template <int B, bool PERM>
 cudaError_t launch_split_resid_reg(const StepArgs &a, cudaStream_t s) {
     static int per_sm = 0;
