@@ -127,9 +127,6 @@ struct FoldArgs {
 
 // ---------------------------------------------------------------- launchers
 // dense kernels (k_dense.cu)
-cudaError_t launch_residual(const int64_t *u_ptr, const int32_t *u_idx, const float *W,
-                            const float *H, const float *y, int32_t n_users, int32_t d,
-                            float *e, cudaStream_t s);
 // e = W H^T - y over the user-side task list (persistent, work-stealing over an
 // atomic counter, which the launcher zeroes on the stream first).
 cudaError_t launch_residual_tasks(const Task *tasks, int32_t n_tasks, const int32_t *u_idx,
@@ -164,8 +161,6 @@ cudaError_t launch_gram_capped(const float *X, int64_t n, int32_t d, int32_t p0,
 int64_t gram64_ws_doubles(int64_t n, int32_t d);
 cudaError_t launch_gram64(const float *X, int64_t n, int32_t d, double *G64, double *ws,
                           cudaStream_t s);
-// Fixed-order sum of nsplit partial d x bs tiles into G.
-cudaError_t launch_gram_reduce(const float *ws, int nsplit, int64_t count, float *G, cudaStream_t s);
 
 // tcgen05 partial Gramian (k_tc_gram.cu): TMA descriptors of one BF16 hi/lo pair
 // (opaque CUtensorMap storage) and the launcher; err receives a nonzero code if

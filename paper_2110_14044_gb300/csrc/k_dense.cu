@@ -25,10 +25,9 @@ __device__ __forceinline__ float dot4(float4 a, float4 b) {
 // once (one coalesced load), then sub-groups of SG = 2^SGL lanes take
 // interactions sub, sub + 32/SG, ...; lane l of a sub-group owns float4 chunks
 // l, l + SG, ... (MAXV of them) of the d-vector.  Each sub-group keeps up to
-// four gathers in flight before it reduces.
-// LOSS = false: write e[s] = <w_u, h_i> - y_s.
-// LOSS = true : accumulate alpha_s (<w_u, h_i> - y_s)^2 in FP64, one partial per block.
-template <int SGL, int MAXV, bool LOSS>
+// four gathers in flight before it reduces.  Each block accumulates
+// alpha_s (<w_u, h_i> - y_s)^2 in FP64 and writes one partial sum.
+template <int SGL, int MAXV>
 __global__ void __launch_bounds__(256) k_residual(const int64_t *__restrict__ u_ptr,
                                                   const int32_t *__restrict__ u_idx,
                                                   const float *__restrict__ W,
@@ -36,7 +35,7 @@ __global__ void __launch_bounds__(256) k_residual(const int64_t *__restrict__ u_
                                                   const float *__restrict__ y,
                                                   const float *__restrict__ alpha,
                                                   int32_t n_users, int32_t d,
-                                                  float *__restrict__ e, double *__restrict__ part) {
+                                                  double *__restrict__ part) {
     constexpr int SG = 1 << SGL, NSUB = 32 / SG;  // NSUB sub-groups, SG interactions each per chunk
     constexpr int UMAX = MAXV >= 16 ? 1 : (MAXV >= 8 ? 2 : 4);  // keep U * MAXV float4 in registers <= 16
     constexpr int U = SG < UMAX ? SG : UMAX;
@@ -88,24 +87,21 @@ __global__ void __launch_bounds__(256) k_residual(const int64_t *__restrict__ u_
                         if (k < cnt) {
                             const int64_t s = s0 + k;
                             const float r = acc[q] - (y ? y[s] : 1.0f);
-                            if (LOSS) loss += (alpha ? (double)alpha[s] : 1.0) * (double)r * (double)r;
-                            else e[s] = r;
+                            loss += (alpha ? (double)alpha[s] : 1.0) * (double)r * (double)r;
                         }
                     }
                 }
             }
         }
     }
-    if (LOSS) {
-        __shared__ double red[256];
-        red[threadIdx.x] = loss;
+    __shared__ double red[256];
+    red[threadIdx.x] = loss;
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
-        for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
-            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) part[blockIdx.x] = red[0];
     }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
 // Residual cache e = W H^T - y over S (Alg. 3, "Compute yhat"), persistent and
@@ -451,11 +447,9 @@ int residual_grid(int32_t n_rows) {
     return g < 4 * kSMs ? (g > 0 ? g : 1) : 4 * kSMs;
 }
 
-template <bool LOSS>
-cudaError_t launch_residual_impl(const int64_t *u_ptr, const int32_t *u_idx, const float *W,
+cudaError_t launch_sq_loss_parts(const int64_t *u_ptr, const int32_t *u_idx, const float *W,
                                  const float *H, const float *y, const float *alpha,
-                                 int32_t n_users, int32_t d, float *e, double *part,
-                                 int grid, cudaStream_t s) {
+                                 int32_t n_users, int32_t d, double *part, int grid, cudaStream_t s) {
     // sub-group size: about four float4 chunks per lane, at most 32 lanes
     const int nv4 = d / 4;
     int sg_log = 0;
@@ -463,8 +457,7 @@ cudaError_t launch_residual_impl(const int64_t *u_ptr, const int32_t *u_idx, con
     const int SG = 1 << sg_log;
     const int maxv = (nv4 + SG - 1) / SG;
 #define IALS_RES(SGL, MV)                                                                    \
-    k_residual<SGL, MV, LOSS><<<grid, 256, 0, s>>>(u_ptr, u_idx, W, H, y, alpha, n_users, d, \
-                                                   e, part)
+    k_residual<SGL, MV><<<grid, 256, 0, s>>>(u_ptr, u_idx, W, H, y, alpha, n_users, d, part)
     // maxv < 8 whenever sg_log < 5 (the loop above stops at 4 chunks per lane)
     if (sg_log == 0) {
         if (maxv <= 1) IALS_RES(0, 1);
@@ -504,21 +497,13 @@ cudaError_t launch_residual_tasks_t(const Task *tasks, int32_t n_tasks, const in
 
 }  // namespace
 
-cudaError_t launch_residual(const int64_t *u_ptr, const int32_t *u_idx, const float *W,
-                            const float *H, const float *y, int32_t n_users, int32_t d,
-                            float *e, cudaStream_t s) {
-    if (n_users == 0) return cudaSuccess;
-    return launch_residual_impl<false>(u_ptr, u_idx, W, H, y, nullptr, n_users, d, e, nullptr,
-                                       residual_grid(n_users), s);
-}
-
 cudaError_t launch_residual_tasks(const Task *tasks, int32_t n_tasks, const int32_t *u_idx,
                                   const float *W, const float *H, const float *y, int32_t d, float *e,
                                   int32_t *counter, cudaStream_t s) {
     if (n_tasks == 0) return cudaSuccess;
     cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
     if (err != cudaSuccess) return err;
-    // same sub-group choice as launch_residual_impl
+    // same sub-group choice as launch_sq_loss_parts
     const int nv4 = d / 4;
     int sg_log = 0;
     while ((2 << sg_log) <= 32 && (2 << sg_log) * 4 <= nv4) ++sg_log;
@@ -548,8 +533,7 @@ cudaError_t launch_sq_loss(const int64_t *u_ptr, const int32_t *u_idx, const flo
                            double *out, cudaStream_t s) {
     int grid = residual_grid(n_users);
     if (grid > n_part) grid = n_part;
-    cudaError_t err = launch_residual_impl<true>(u_ptr, u_idx, W, H, y, alpha, n_users, d,
-                                                 nullptr, part, grid, s);
+    cudaError_t err = launch_sq_loss_parts(u_ptr, u_idx, W, H, y, alpha, n_users, d, part, grid, s);
     if (err != cudaSuccess) return err;
     k_sum_parts<<<1, 256, 0, s>>>(part, grid, 1.0, out, 0);
     return cudaGetLastError();
@@ -628,11 +612,6 @@ cudaError_t launch_gram_reduce_cols(const float *ws, int nsplit, int32_t rows, i
                                     int32_t col0, cudaStream_t s) {
     const int64_t count = (int64_t)rows * cols;
     k_gram_reduce_cols<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(ws, nsplit, rows, cols, G, ldg, col0);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_gram_reduce(const float *ws, int nsplit, int64_t count, float *G, cudaStream_t s) {
-    k_gram_reduce<float><<<(unsigned)((count + 255) / 256), 256, 0, s>>>(ws, nsplit, count, G);
     return cudaGetLastError();
 }
 
