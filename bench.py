@@ -55,10 +55,10 @@ NCU_TRAFFIC = {
     ("sparse", "bf16"): {"workload": ("ml20m_136k", 128, 32),
                          "sources": ["paper_2110_14044_gb300/csrc/k_sparse_bf16.cuh",
                                      "paper_2110_14044_gb300/csrc/k_sparse_impl.cuh"],
-                         "sha256_16": "cc2b5665578fcdd8", "bytes_per_launch": 278.9e6},
+                         "sha256_16": "0594d0c78e6f6c8a", "bytes_per_launch": 285.9e6},
     ("sparse", "fp32"): {"workload": ("ml20m_136k", 128, 32),
                          "sources": ["paper_2110_14044_gb300/csrc/k_sparse_impl.cuh"],
-                         "sha256_16": "e27bf5a1bfe2cae8", "bytes_per_launch": 182.0e6},
+                         "sha256_16": "c13815dc33e98630", "bytes_per_launch": 180.3e6},
 }
 
 

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) gac[t][q] = 0.f;
         int cB = 0;
-        int64_t qB = 0, q0 = 0;
+        int64_t qB = 0;
         float eB = 0.f;
         auto load_meta = [&](int j) {
             const int cnt = min(CH, tk.len - j * CH);
@@ -212,14 +212,15 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
             gather_hilo<B>(th, tl, a, cB, cnt, lane);
             cp_async_commit();
         };
+        // chunk ch is staged in buffer (nch - 1 - ch) & 1, so the last chunk ends in
+        // buffer 0, which the solve leaves intact: the residual update starts with it
         if (nch > 0) {
             load_meta(0);
-            q0 = qB;
-            issue(0, 0);
+            issue(0, (nch - 1) & 1);
             if (nch > 1) load_meta(1);
         }
         for (int ch = 0; ch < nch; ++ch) {
-            const int bi = ch & 1;
+            const int bi = (nch - 1 - ch) & 1;
             cp_async_wait_all();
             __syncwarp();
             if (ch + 1 < nch) {
@@ -319,42 +320,48 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
         __syncwarp();
         unsigned dh[MT][2], dl[MT][2];
         delta_frags<B>(vv, lane, dh, dl);
-        if (nch == 1) {  // the slices are still in buffer 0
-            const __nv_bfloat16 *th = th_of(0), *tl = th + C::TILE;
-            const float pr = project_mma<B>(th, tl, (tk.len + 15) >> 4, dh, dl, lane);
-            if (lane < tk.len) a.e[q0] -= pr;
-            __syncwarp();
-        } else if (nch > 1) {
-            int64_t qc = 0;
-            auto meta2 = [&](int j) {
-                const int cnt = min(CH, tk.len - j * CH);
-                if (lane < cnt) {
-                    const int64_t s = tk.begin + (int64_t)j * CH + lane;
-                    cB = a.idx[s];
-                    qB = PERM ? (int64_t)a.pos[s] : s;
-                }
+        if (nch > 0) {
+            // the last chunk is projected from buffer 0 while chunks 0 .. nch - 2
+            // are re-gathered into alternating buffers
+            const int clast = tk.len - (nch - 1) * CH;
+            int64_t qlast = 0;
+            if (lane < clast) {
+                const int64_t s = tk.begin + (int64_t)(nch - 1) * CH + lane;
+                qlast = PERM ? (int64_t)a.pos[s] : s;
+            }
+            auto meta2 = [&](int j) {  // chunks before the last are full
+                const int64_t s = tk.begin + (int64_t)j * CH + lane;
+                cB = a.idx[s];
+                qB = PERM ? (int64_t)a.pos[s] : s;
             };
-            meta2(0);
-            qc = qB;
-            gather_hilo<B>(th_of(0), th_of(0) + C::TILE, a, cB, min(CH, tk.len), lane);
-            cp_async_commit();
-            meta2(1);
-            for (int ch = 0; ch < nch; ++ch) {
-                const int bi = ch & 1;
+            int64_t qc = 0;
+            if (nch > 1) {
+                meta2(0);
+                qc = qB;
+                gather_hilo<B>(th_of(1), th_of(1) + C::TILE, a, cB, CH, lane);
+                cp_async_commit();
+                if (nch > 2) meta2(1);
+            }
+            {
+                const __nv_bfloat16 *th = th_of(0), *tl = th + C::TILE;
+                const float pr = project_mma<B>(th, tl, (clast + 15) >> 4, dh, dl, lane);
+                if (lane < clast) a.e[qlast] -= pr;
+                __syncwarp();
+            }
+            for (int ch = 0; ch + 1 < nch; ++ch) {  // chunk ch sits in buffer (ch + 1) & 1
+                const int bi = (ch + 1) & 1;
                 cp_async_wait_all();
                 __syncwarp();
                 int64_t qn = 0;
-                if (ch + 1 < nch) {
-                    gather_hilo<B>(th_of(bi ^ 1), th_of(bi ^ 1) + C::TILE, a, cB,
-                                   min(CH, tk.len - (ch + 1) * CH), lane);
+                if (ch + 2 < nch) {
+                    gather_hilo<B>(th_of(bi ^ 1), th_of(bi ^ 1) + C::TILE, a, cB, CH, lane);
                     cp_async_commit();
                     qn = qB;
-                    if (ch + 2 < nch) meta2(ch + 2);
+                    if (ch + 3 < nch) meta2(ch + 2);
                 }
-                const int cnt = min(CH, tk.len - ch * CH);
                 const __nv_bfloat16 *th = th_of(bi), *tl = th + C::TILE;
-                const float pr = project_mma<B>(th, tl, (cnt + 15) >> 4, dh, dl, lane);
-                if (lane < cnt) a.e[qc] -= pr;
+                const float pr = project_mma<B>(th, tl, 2, dh, dl, lane);  // a full chunk
+                a.e[qc] -= pr;
                 __syncwarp();
                 qc = qn;
             }

@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
         }
         // chunk meta in registers: column id, residual index, residual, weight
         int cB = 0;
-        int64_t qB = 0, q0 = 0;
+        int64_t qB = 0;
         float eB = 0.f, aB = 1.f;
         auto load_meta = [&](int j) {
             const int cnt = min(CH, tk.len - j * CH);
@@ -519,14 +519,15 @@ __global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
             if (HAS_A) sha[bi * CH + lane] = aB;
             cp_async_commit();
         };
+        // chunk ch is staged in buffer (nch - 1 - ch) & 1, so the last chunk ends in
+        // buffer 0, which the solve leaves intact: the residual update starts with it
         if (nch > 0) {
             load_meta(0);
-            q0 = qB;
-            issue(0, 0);
+            issue(0, (nch - 1) & 1);
             if (nch > 1) load_meta(1);
         }
         for (int ch = 0; ch < nch; ++ch) {
-            const int bi = ch & 1;
+            const int bi = (nch - 1 - ch) & 1;
             cp_async_wait_all();
             __syncwarp();
             if (ch + 1 < nch) {
@@ -610,39 +611,42 @@ __global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
         __syncwarp();
         if (sub == 0) vv[col] = delta;
         __syncwarp();
-        if (nch == 1) {  // the slices are still in buffer 0
-            if (lane < tk.len) a.e[q0] -= dot_slice<B>(vv, wbase + lane * SB);
-            __syncwarp();
-        } else if (nch > 1) {
-            int64_t qc = 0;
-            // meta one chunk ahead, slices double-buffered
+        if (nch > 0) {
+            // the last chunk is projected from buffer 0 while chunks 0 .. nch - 2
+            // (full chunks) are re-gathered into alternating buffers
+            const int clast = tk.len - (nch - 1) * CH;
+            int64_t qlast = 0;
+            if (lane < clast) {
+                const int64_t s = tk.begin + (int64_t)(nch - 1) * CH + lane;
+                qlast = PERM ? (int64_t)a.pos[s] : s;
+            }
             auto meta2 = [&](int j) {
-                const int cnt = min(CH, tk.len - j * CH);
-                if (lane < cnt) {
-                    const int64_t s = tk.begin + (int64_t)j * CH + lane;
-                    cB = a.idx[s];
-                    qB = PERM ? (int64_t)a.pos[s] : s;
-                }
+                const int64_t s = tk.begin + (int64_t)j * CH + lane;
+                cB = a.idx[s];
+                qB = PERM ? (int64_t)a.pos[s] : s;
             };
-            meta2(0);
-            qc = qB;
-            gather_async<B>(wbase, a.F, a.d, a.p0, cB, min(CH, tk.len), lane);
-            cp_async_commit();
-            meta2(1);
-            for (int ch = 0; ch < nch; ++ch) {
-                const int bi = ch & 1;
+            int64_t qc = 0;
+            if (nch > 1) {
+                meta2(0);
+                qc = qB;
+                gather_async<B>(wbase + C::BUF, a.F, a.d, a.p0, cB, CH, lane);
+                cp_async_commit();
+                if (nch > 2) meta2(1);
+            }
+            if (lane < clast) a.e[qlast] -= dot_slice<B>(vv, wbase + lane * SB);
+            __syncwarp();
+            for (int ch = 0; ch + 1 < nch; ++ch) {  // chunk ch sits in buffer (ch + 1) & 1
+                const int bi = (ch + 1) & 1;
                 cp_async_wait_all();
                 __syncwarp();
                 int64_t qn = 0;
-                if (ch + 1 < nch) {
-                    gather_async<B>(wbase + (bi ^ 1) * C::BUF, a.F, a.d, a.p0, cB,
-                                    min(CH, tk.len - (ch + 1) * CH), lane);
+                if (ch + 2 < nch) {
+                    gather_async<B>(wbase + (bi ^ 1) * C::BUF, a.F, a.d, a.p0, cB, CH, lane);
                     cp_async_commit();
                     qn = qB;
-                    if (ch + 2 < nch) meta2(ch + 2);
+                    if (ch + 3 < nch) meta2(ch + 2);
                 }
-                const int cnt = min(CH, tk.len - ch * CH);
-                if (lane < cnt) a.e[qc] -= dot_slice<B>(vv, wbase + bi * C::BUF + lane * SB);
+                a.e[qc] -= dot_slice<B>(vv, wbase + bi * C::BUF + lane * SB);
                 __syncwarp();
                 qc = qn;
             }
