@@ -115,9 +115,12 @@ ials_status ials_objective(ials_ctx *ctx, double *out);
 /* Copy W (n_users x d) and/or H (n_items x d) out; either pointer may be NULL. */
 ials_status ials_get_factors(ials_ctx *ctx, float *W, float *H);
 
-/* Overwrite W and/or H (either may be NULL) and recompute the residual cache
- * from them; used to resume from a checkpoint taken at an epoch boundary
- * (Algorithm 3 recomputes the cache per epoch, so resuming is exact). */
+/* Overwrite W and/or H (either may be NULL); the residual cache is recomputed
+ * from them before it is next read (an epoch recomputes it first anyway, and
+ * ials_block_step / ials_get_residuals do so when the factors were replaced).
+ * Used to resume from a checkpoint taken at an epoch boundary (Algorithm 3
+ * recomputes the cache per epoch, so resuming is exact).  The host buffers
+ * may be reused when the call returns. */
 ials_status ials_set_factors(ials_ctx *ctx, const float *W, const float *H);
 
 /* --- single steps of Algorithm 3 (for step-level checks and profiling) --- */

@@ -144,6 +144,7 @@ struct ials_ctx {
     double *g64a = nullptr, *g64b = nullptr, *g64ws = nullptr;
     cudaGraphExec_t graph = nullptr;
     bool own_stream = false;
+    bool e_stale = false;  // W or H replaced since the residual cache was last computed
     // per side, for the work model: interactions in unsplit rows / split rows,
     // number of unsplit rows, split rows, partial slots, tasks
     int64_t nnz_unsplit[2] = {0, 0}, nnz_split[2] = {0, 0};
@@ -228,6 +229,15 @@ ials_status upload(ials_ctx *c, const void *src, void *dst, size_t bytes, const 
 cudaError_t residual_enqueue(ials_ctx *c) {
     return launch_residual_tasks(c->side[0].tasks, c->side[0].n_tasks, c->side[0].idx, c->W, c->H, c->y,
                                  c->p.d, c->e, c->ctl, c->stream);
+}
+
+// After ials_set_factors the cache is rebuilt lazily: every epoch starts with
+// its own recompute, so only the calls that read it outside an epoch rebuild it.
+cudaError_t ensure_residuals(ials_ctx *c) {
+    if (!c->e_stale) return cudaSuccess;
+    cudaError_t err = residual_enqueue(c);
+    if (err == cudaSuccess) c->e_stale = false;
+    return err;
 }
 
 cudaError_t launch_sparse_bf16(int32_t b, const StepArgs &a, cudaStream_t s) {
@@ -636,6 +646,7 @@ ials_status ials_epoch(ials_ctx *c, int32_t n_epochs, double *objective_after) {
             if (st != IALS_OK) return st;
         }
     }
+    if (n_epochs > 0) c->e_stale = false;  // each epoch recomputed the cache first
     ials_status st = finish(c);
     if (objective_after && (st == IALS_OK || st == IALS_ENOTPD)) {
         ials_status s2 = objective_enqueue(c);
@@ -671,8 +682,8 @@ ials_status ials_set_factors(ials_ctx *c, const float *W, const float *H) {
         IALS_CUDA(launch_split_bf16(c->W, (int64_t)c->n_users * c->p.d, c->Wh, c->Wl, c->stream), "W shadow");
     if (H && c->Hh)
         IALS_CUDA(launch_split_bf16(c->H, (int64_t)c->n_items * c->p.d, c->Hh, c->Hl, c->stream), "H shadow");
-    // the residual cache is a function of W and H: keep it consistent
-    IALS_CUDA(residual_enqueue(c), "residual recompute");
+    // the residual cache is a function of W and H: rebuilt before it is next read
+    c->e_stale = true;
     IALS_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
     return IALS_OK;
 }
@@ -680,6 +691,7 @@ ials_status ials_set_factors(ials_ctx *c, const float *W, const float *H) {
 ials_status ials_recompute_residuals(ials_ctx *c) {
     if (!c) return fail(IALS_EINVAL, "bad context");
     IALS_CUDA(residual_enqueue(c), "residual recompute");
+    c->e_stale = false;
     IALS_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
     return IALS_OK;
 }
@@ -688,6 +700,7 @@ ials_status ials_block_step(ials_ctx *c, int32_t side, int32_t block) {
     if (!c || side < 0 || side > 1 || block < 0 || block >= c->p.d / c->p.b)
         return fail(IALS_EINVAL, "bad side or block");
     IALS_CUDA(cudaMemsetAsync(c->stats, 0, 2 * sizeof(int64_t), c->stream), "stats reset");
+    IALS_CUDA(ensure_residuals(c), "residual recompute");
     ials_status st = step_enqueue(c, side, block);
     if (st != IALS_OK) return st;
     return finish(c);
@@ -695,6 +708,7 @@ ials_status ials_block_step(ials_ctx *c, int32_t side, int32_t block) {
 
 ials_status ials_get_residuals(ials_ctx *c, float *e) {
     if (!c || !e) return fail(IALS_EINVAL, "bad arguments");
+    IALS_CUDA(ensure_residuals(c), "residual recompute");
     IALS_CUDA(cudaMemcpyAsync(e, c->e, sizeof(float) * (size_t)c->nnz, cudaMemcpyDefault, c->stream),
               "copy residuals out");
     IALS_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
@@ -722,6 +736,7 @@ ials_status ials_profile_epochs(ials_ctx *c, int32_t n_epochs, double *kernel_ms
         ials_status st = epoch_enqueue(c, &prof);
         if (st != IALS_OK) return st;
     }
+    if (n_epochs > 0) c->e_stale = false;
     prof_mark(&prof, -1, c->stream);
     ials_status st = finish(c);
     if (st != IALS_OK && st != IALS_ENOTPD) return st;

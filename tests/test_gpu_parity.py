@@ -336,6 +336,30 @@ def test_set_factors_refreshes_residual_cache():
     np.testing.assert_allclose(e, oracle.predict(P, prob.W0, prob.H0) - 1.0, rtol=1e-5, atol=1e-6)
 
 
+def test_block_step_right_after_set_factors():
+    """Replacing the factors marks the residual cache stale; a block step issued
+    next (no epoch, no explicit recompute) must rebuild it from the new factors."""
+    d, b = 16, 8
+    prob = small(d=d, seed=16)
+    m = Model(prob.data, d, b, 0.1, 1e-3, W0=prob.W0, H0=prob.H0)
+    assert m.block_step(0, 0) == 0
+    rng = np.random.default_rng(17)
+    W1 = (0.1 * rng.standard_normal(prob.W0.shape)).astype(np.float32)
+    H1 = (0.1 * rng.standard_normal(prob.H0.shape)).astype(np.float32)
+    m.set_factors(W1, H1)
+    P = oracle.Problem.from_data(prob.data, d, b, 0.1, 1e-3)
+    W, H = P.factors(W1, H1)
+    yhat = oracle.predict(P, W, H)
+    for side in (0, 1):
+        assert m.block_step(side, 1) == 0
+        assert oracle.halfstep(P, side, 1, W, H, yhat) == 0
+        Wg, Hg = m.factors()
+        assert rel_embed_err(Wg, W) <= STEP_TOL, side
+        assert rel_embed_err(Hg, H) <= STEP_TOL, side
+    e = m.residuals().astype(np.float64)
+    assert np.abs(e - (yhat - 1.0)).max() <= STEP_TOL * np.abs(yhat - 1.0).max()
+
+
 @pytest.mark.parametrize("d,b", [(4, 4), (20, 4), (48, 16), (100, 4), (1024, 32)])
 def test_unusual_dimensions(d, b):
     prob = small(d=d, seed=16)
