@@ -55,10 +55,10 @@ NCU_TRAFFIC = {
     ("sparse", "bf16"): {"workload": ("ml20m_136k", 128, 32),
                          "sources": ["paper_2110_14044_gb300/csrc/k_sparse_bf16.cuh",
                                      "paper_2110_14044_gb300/csrc/k_sparse_impl.cuh"],
-                         "sha256_16": "0594d0c78e6f6c8a", "bytes_per_launch": 285.9e6},
+                         "sha256_16": "649ef0cd0d70fba4", "bytes_per_launch": 287.8e6},
     ("sparse", "fp32"): {"workload": ("ml20m_136k", 128, 32),
                          "sources": ["paper_2110_14044_gb300/csrc/k_sparse_impl.cuh"],
-                         "sha256_16": "c13815dc33e98630", "bytes_per_launch": 180.3e6},
+                         "sha256_16": "d5231016883d3cc7", "bytes_per_launch": 183.2e6},
 }
 
 

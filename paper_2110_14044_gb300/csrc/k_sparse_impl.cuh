@@ -119,6 +119,24 @@ __device__ __forceinline__ void stage_chunk(const StepArgs &a, int64_t begin, in
     __syncwarp();
 }
 
+// Packed FP32 pairs (fma / mul .rn.f32x2, sm_100 and later): two independent
+// FP32 operations, each rounded exactly as its scalar form, issued as one
+// instruction.  fma2: d = a * b + d; mul2: d = d * a.
+__device__ __forceinline__ void fma2(float &d0, float &d1, float a0, float a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rd, {%0, %1};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rd;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void mul2(float &d0, float &d1, float a0, float a1) {
+    asm("{\n\t.reg .b64 ra, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rd, {%0, %1};\n\t"
+        "mul.rn.f32x2 rd, rd, ra;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a0), "f"(a1));
+}
+
 // Approximate reciprocal (rcp.approx: at most 1 ulp from 1/x).
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
@@ -194,12 +212,15 @@ __device__ __forceinline__ bool gj_solve2(float (&A)[B], float g, int col, int s
         }
 #pragma unroll
         for (int j0 = (k + 2) & ~3; j0 < B; j0 += 4) {
+            // k is even, so the entries j > k + 1 start at a pair boundary
             const float4 q1 = *reinterpret_cast<const float4 *>(v1 + j0);
             const float4 q2 = *reinterpret_cast<const float4 *>(v2 + j0);
-            if (j0 > k + 1) A[j0] -= s1 * q1.x + s2 * q2.x;
-            if (j0 + 1 > k + 1) A[j0 + 1] -= s1 * q1.y + s2 * q2.y;
-            if (j0 + 2 > k + 1) A[j0 + 2] -= s1 * q1.z + s2 * q2.z;
-            A[j0 + 3] -= s1 * q1.w + s2 * q2.w;
+            if (j0 > k + 1) {
+                fma2(A[j0], A[j0 + 1], -s1, -s1, q1.x, q1.y);
+                fma2(A[j0], A[j0 + 1], -s2, -s2, q2.x, q2.y);
+            }
+            fma2(A[j0 + 2], A[j0 + 3], -s1, -s1, q1.z, q1.w);
+            fma2(A[j0 + 2], A[j0 + 3], -s2, -s2, q2.z, q2.w);
         }
         g -= s1 * g1 + s2 * g2;
     }
@@ -545,16 +566,21 @@ __global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
                 load_seg<T>(xk + T * tj, xb);
                 const float ek = be[k];
 #pragma unroll
-                for (int i = 0; i < T; ++i) gacc[i] += ek * xa[i];
+                for (int i = 0; i < T; i += 2) fma2(gacc[i], gacc[i + 1], ek, ek, xa[i], xa[i + 1]);
                 if (HAS_A) {
                     const float ak = ba[k];
 #pragma unroll
-                    for (int i = 0; i < T; ++i) xa[i] *= ak;
+                    for (int i = 0; i < T; i += 2) mul2(xa[i], xa[i + 1], ak, ak);
                 }
+                // pairs (i, j), (i + 1, j + 1) and (i, j + 1), (i + 1, j): both
+                // operands are adjacent pairs of the staged slices
 #pragma unroll
-                for (int i = 0; i < T; ++i)
+                for (int i = 0; i < T; i += 2)
 #pragma unroll
-                    for (int j = 0; j < T; ++j) acc[i][j] += xa[i] * xb[j];
+                    for (int j = 0; j < T; j += 2) {
+                        fma2(acc[i][j], acc[i + 1][j + 1], xa[i], xa[i + 1], xb[j], xb[j + 1]);
+                        fma2(acc[i][j + 1], acc[i + 1][j], xa[i], xa[i + 1], xb[j + 1], xb[j]);
+                    }
             }
             __syncwarp();
         }
@@ -603,7 +629,7 @@ __global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
         for (int j = 0; j < B; ++j) A[j] += sGpp[j * B + col] + (j == col ? lam : 0.f);
         g += a.R[(int64_t)row * B + col];
         float delta;
-        if (!chol_solve<B>(A, g, col, sub, w, a.force_fp64 != 0, delta)) {
+        if (!gj_solve2<B>(A, g, col, sub, w, a.force_fp64 != 0, delta)) {
             queue_retry(a, lane, row);
             continue;
         }
