@@ -240,8 +240,9 @@ ials_status ials_foldin_submit(ials_srv *srv, const int32_t *items, const float 
  * IALS_OK, w_out (host, d floats) receives the embedding and the ticket is
  * released.  IALS_EAGAIN: not ready (timeout_us <= 0); IALS_ETIMEDOUT: not ready
  * within timeout_us; IALS_ENOTFOUND: unknown or already collected ticket;
- * IALS_ENOTPD: a block Hessian was not positive definite (ticket released).
- * Thread-safe. */
+ * IALS_ENOTPD: a block Hessian was not positive definite (ticket released);
+ * IALS_ECUDA: the batch holding the request failed on the device (ticket
+ * released).  Thread-safe. */
 ials_status ials_foldin_poll(ials_srv *srv, uint64_t ticket, float *w_out, int32_t timeout_us);
 
 /* ials_foldin_poll that also returns, in *latency_us (if non-NULL), the time
@@ -250,7 +251,8 @@ ials_status ials_foldin_poll(ials_srv *srv, uint64_t ticket, float *w_out, int32
 ials_status ials_foldin_poll_timed(ials_srv *srv, uint64_t ticket, float *w_out, int32_t timeout_us,
                                    double *latency_us);
 
-/* Stop the scheduler, drop queued requests and release everything (NULL: no-op). */
+/* Stop the scheduler, drop queued requests and release everything (NULL: no-op).
+ * No other thread may be inside ials_foldin_submit / _poll on srv meanwhile. */
 ials_status ials_foldin_close(ials_srv *srv);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -150,6 +150,21 @@ struct ials_srv {
         s.busy = false;
     }
 
+    // A batch whose stream reported an error: its requests finish with IALS_ECUDA
+    // (instead of staying pending), and its memory returns to the arena.
+    void fail_slot(Slot &s, cudaError_t err) {
+        error = std::string("fold-in batch: ") + cudaGetErrorString(err);
+        const auto now = std::chrono::steady_clock::now();
+        for (auto &r : s.reqs) {
+            r->t_done = now;
+            r->status = IALS_ECUDA;
+            r->done = true;
+        }
+        alloc.release(s.off, s.bytes);
+        s.reqs.clear();
+        s.busy = false;
+    }
+
     // Build and launch one batch on slot s from the head of the queue.  Caller holds mu.
     bool launch(Slot &s) {
         size_t total = 0, in_bytes = 0;
@@ -255,7 +270,9 @@ struct ials_srv {
             error = std::string("fold-in launch: ") + cudaGetErrorString(e);
             cudaGetLastError();
             cudaStreamSynchronize(s.stream);
+            const auto now = std::chrono::steady_clock::now();
             for (auto &r : s.reqs) {
+                r->t_done = now;
                 r->status = IALS_ECUDA;
                 r->done = true;
             }
@@ -276,8 +293,13 @@ struct ials_srv {
         while (!stop) {
             bool progressed = false;
             for (Slot &s : slots) {
-                if (s.busy && cudaEventQuery(s.ev) == cudaSuccess) {
+                if (!s.busy) continue;
+                const cudaError_t q = cudaEventQuery(s.ev);
+                if (q == cudaSuccess) {
                     retire(s);
+                    progressed = true;
+                } else if (q != cudaErrorNotReady) {
+                    fail_slot(s, q);
                     progressed = true;
                 }
             }
@@ -432,6 +454,7 @@ ials_status ials_foldin_poll_timed(ials_srv *s, uint64_t ticket, float *w_out, i
     const int st = r->status;
     s->table.erase(it);
     if (st == 4) return sfail(IALS_ENOTPD, "a block Hessian was not positive definite");
+    if (st == IALS_ECUDA) return sfail(IALS_ECUDA, s->error.empty() ? "fold-in batch failed" : s->error);
     if (st != 0) return sfail((ials_status)st, "fold-in failed");
     return IALS_OK;
 }
