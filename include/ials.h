@@ -91,7 +91,7 @@ typedef struct {
  * item-major view; if non-NULL it must hold exactly the same pairs (any order
  * within a row), else IALS_EINVAL.  If NULL the library builds it.
  * y and alpha are per interaction in user-major order; NULL means all ones
- * (binary implicit feedback).  alpha must be > 0.
+ * (binary implicit feedback).  alpha must be finite and > 0, y finite.
  * nnz must be < 2^31.  cuda_stream is a cudaStream_t (see the stream convention above).
  * On success *out receives the context; W and H hold the seeded initial draw. */
 ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_items,

@@ -450,7 +450,11 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
         }
     }
     std::vector<float> hy, ha;
-    if (y && (st = fetch(y, nnz, hy, "y")) != IALS_OK) return st;
+    if (y) {
+        if ((st = fetch(y, nnz, hy, "y")) != IALS_OK) return st;
+        for (float v : hy)
+            if (!std::isfinite(v)) return fail(IALS_EINVAL, "y must be finite");
+    }
     if (alpha) {
         if ((st = fetch(alpha, nnz, ha, "alpha")) != IALS_OK) return st;
         for (float v : ha)

@@ -60,3 +60,69 @@ def test_create_fails_loudly_without_device_or_with_bad_args():
     with pytest.raises(_abi.IalsError) as ei:
         _abi.ials_create(p, 2, 2, np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32))
     assert ei.value.status == _abi.EINVAL
+
+
+def _create(p, n_users, n_items, uptr, uidx, **kw):
+    import numpy as np
+    return _abi.ials_create(p, n_users, n_items, np.asarray(uptr, np.int64), np.asarray(uidx, np.int32), **kw)
+
+
+@pytest.mark.parametrize("case", ["d", "b_not_dividing", "bf16_b", "bf16_weighted", "alpha0",
+                                  "indptr_end", "indptr_order", "item_range", "repeat",
+                                  "transpose_len", "transpose_pairs", "alpha_zero", "y_nan"])
+def test_create_validates_on_the_host(case):
+    """Every argument check runs on the host before any device work, so a bad
+    input is rejected with IALS_EINVAL and a message, GPU or not."""
+    import numpy as np
+    fp32, bf16 = _abi.PREC_FP32, _abi.PREC_BF16
+    good = dict(p=_abi.make_params(16, 8, 0.1, 0.01), n_users=3, n_items=4,
+                uptr=[0, 2, 3, 5], uidx=[0, 1, 3, 1, 2])
+    kw = {}
+    if case == "d":
+        good["p"] = _abi.make_params(18, 2, 0.1, 0.01)
+    elif case == "b_not_dividing":
+        good["p"] = _abi.make_params(16, 32, 0.1, 0.01)
+    elif case == "bf16_b":
+        good["p"] = _abi.make_params(16, 8, 0.1, 0.01, precision=bf16)
+    elif case == "bf16_weighted":
+        good["p"] = _abi.make_params(32, 16, 0.1, 0.01, precision=bf16)
+        kw["alpha"] = np.ones(5, np.float32)
+    elif case == "alpha0":
+        good["p"] = _abi.make_params(16, 8, -0.1, 0.01)
+    elif case == "indptr_end":
+        good["uptr"] = [1, 2, 3, 5]  # must start at 0
+    elif case == "indptr_order":
+        good["uptr"] = [0, 3, 2, 5]
+    elif case == "item_range":
+        good["uidx"] = [0, 1, 4, 1, 2]
+    elif case == "repeat":
+        good["uidx"] = [1, 1, 3, 1, 2]
+    elif case == "transpose_len":
+        kw["i_indptr"] = np.array([0, 1, 2, 4, 5], np.int64)
+        kw["i_users"] = np.array([0, 0, 1, 2, 0], np.int32)
+    elif case == "transpose_pairs":
+        # item-major view of the same lengths but a wrong user for item 3
+        kw["i_indptr"] = np.array([0, 1, 3, 4, 5], np.int64)
+        kw["i_users"] = np.array([0, 0, 1, 2, 1], np.int32)
+    elif case == "alpha_zero":
+        kw["alpha"] = np.array([1, 1, 0, 1, 1], np.float32)
+    elif case == "y_nan":
+        kw["y"] = np.array([1, np.nan, 1, 1, 1], np.float32)
+    with pytest.raises(_abi.IalsError) as ei:
+        _create(**good, **kw)
+    assert ei.value.status == _abi.EINVAL, (case, str(ei.value))
+
+
+def test_create_accepts_valid_input_up_to_the_device_check():
+    """The same (valid) arguments pass every host check; without an sm_103a
+    device the call then fails with IALS_ECUDA, never silently on the CPU."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    p = _abi.make_params(16, 8, 0.1, 0.01)
+    with pytest.raises(_abi.IalsError) as ei:
+        _create(p, 3, 4, [0, 2, 3, 5], [0, 1, 3, 1, 2],
+                i_indptr=np.array([0, 1, 3, 4, 5], np.int64), i_users=np.array([0, 2, 0, 2, 1], np.int32),
+                y=np.ones(5, np.float32), alpha=np.full(5, 2.0, np.float32))
+    assert ei.value.status == _abi.ECUDA, str(ei.value)
