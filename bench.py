@@ -121,6 +121,19 @@ def job_throughput(units_per_rank, world, ms_max):
     return world * units_per_rank / (ms_max / 1e3)
 
 
+def launches_per_epoch(kern, steps, bf16, b):
+    """Kernel launches per epoch from the profiled intervals ({kind: (ms, marks)}).
+
+    Every interval holds one kernel except the Gramian and row-term ones: the
+    FP32 Gramian is a tile kernel and a reduction, the FP32 row terms one
+    kernel; on the BF16 path each 32-column slab (one for b = 16, 32; b / 32
+    above) is a tcgen05 kernel plus a reduction (Gramian) or plus the G
+    transpose-split (row terms)."""
+    slabs = max(1, b // 32) if bf16 else 1
+    per_mark = {"gram": 2 * slabs, "rowterm": 2 * slabs if bf16 else 1}
+    return sum(c * per_mark.get(k, 1) for k, (_, c) in kern.items()) / steps
+
+
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
@@ -296,8 +309,7 @@ def run_ours(args):
     # per-kernel device times over the same number of eager epochs (events per launch)
     kern, prof_total, _ = _abi.ials_profile_epochs(m.ctx, args.steps)
     work = _abi.ials_work_model(m.ctx)
-    launches_per_epoch = sum(c for _, c in kern.values()) / args.steps + \
-        kern["gram"][1] / args.steps  # each Gramian mark covers a tile and a reduce kernel
+    n_launch_epoch = launches_per_epoch(kern, args.steps, prec == _abi.PREC_BF16, prob.b)
     dom = max(("sparse", "gram", "rowterm", "residual", "split_solve", "split_resid"),
               key=lambda k: kern[k][0])
     peaks = {}
@@ -368,7 +380,7 @@ def run_ours(args):
         "kernels_roofline": per_kind,
         "e2e": {"value": job_throughput(rows_per_epoch, world, e2e_ms), "unit": "rows/s",
                 "h2d_bytes_per_step": fb, "d2h_bytes_per_step": fb, "ms_per_step": e2e_ms},
-        "gpu_launches": int(round(launches_per_epoch * args.steps)),
+        "gpu_launches": int(round(n_launch_epoch * args.steps)),
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -57,3 +57,21 @@ def test_foldin_requests_follow_the_recipe():
     # Zipf popularity: item 0 (the most popular here) is in far more histories than item 40,000
     counts = np.bincount(np.concatenate(reqs), minlength=n_items)
     assert counts[0] > 10 * max(1, counts[40000])
+
+
+def test_launch_count_per_epoch_matches_the_kernel_structure():
+    """ML20M shape, d = 128, b = 32 (4 blocks, both sides split long rows): the
+    ncu launch list of a BF16 epoch holds 65 kernels (sparse, split solve,
+    split residual, retry, tcgen05 Gramian, its reduction, G transpose-split
+    and tcgen05 row terms 8 each, one residual recompute)."""
+    steps = 3
+    marks = {"residual": 1, "gram": 8, "rowterm": 8, "sparse": 8, "split_solve": 8,
+             "split_resid": 8, "retry": 8, "objective": 0}
+    kern = {k: (1.0, c * steps) for k, c in marks.items()}
+    assert bench.launches_per_epoch(kern, steps, True, 32) == 65
+    # FP32: Gramian tile + reduction, one row-term kernel
+    assert bench.launches_per_epoch(kern, steps, False, 32) == 57
+    # BF16 at b = 128 = d: one block, 4 slabs of 32 columns per Gramian and row term
+    marks1 = dict(marks, gram=2, rowterm=2, sparse=2, split_solve=2, split_resid=2, retry=2)
+    kern1 = {k: (1.0, c) for k, c in marks1.items()}
+    assert bench.launches_per_epoch(kern1, 1, True, 128) == 1 + 2 * 8 + 2 * 8 + 4 * 2
