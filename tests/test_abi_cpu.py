@@ -126,3 +126,13 @@ def test_create_accepts_valid_input_up_to_the_device_check():
                 i_indptr=np.array([0, 1, 3, 4, 5], np.int64), i_users=np.array([0, 2, 0, 2, 1], np.int32),
                 y=np.ones(5, np.float32), alpha=np.full(5, 2.0, np.float32))
     assert ei.value.status == _abi.ECUDA, str(ei.value)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library every call raises; nothing falls back to the CPU."""
+    monkeypatch.setattr(_abi, "_lib", None)
+    monkeypatch.setattr(_abi, "LIB_PATH", str(tmp_path / "libials.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        _abi.ials_last_error()
+    with pytest.raises(RuntimeError, match="missing"):
+        _abi.ials_create(_abi.make_params(16, 8, 0.1, 0.01), 1, 1, [0, 0], [])
