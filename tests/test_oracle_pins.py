@@ -369,3 +369,21 @@ def test_rows_step_matches_row_step():
         s1, w1 = oracle.row_step(P, 1, 2, W1, H1, yhat, r)
         assert st[k] == s1 == 0
         np.testing.assert_array_equal(out[k], w1)
+
+
+@pytest.mark.parametrize("b", [1, 2, 4])
+def test_epochs_reach_a_stationary_point_of_the_loss(b):
+    """Iterated to convergence, Algorithm 3 stops where the whole brute-force
+    gradient of Eq. 2 vanishes (every coordinate of W and H, not only the
+    block just solved), from b = 1 (iCD) through b = d (iALS)."""
+    data, y, alpha, W, H = tiny(seed=21, d=4)
+    a0, lam, nu = 0.2, 0.1, 0.3
+    P = make(data, y, alpha, 4, b, a0, lam, nu)
+    W1, H1, _, trace, st = oracle.ialspp(P, 400, W, H, trace=True)
+    assert st == 0
+    gW = fd_grad(lambda v: brute_loss(data, y, alpha, v.reshape(W1.shape), H1, a0, lam, nu),
+                 W1.ravel().copy(), range(W1.size))
+    gH = fd_grad(lambda v: brute_loss(data, y, alpha, W1, v.reshape(H1.shape), a0, lam, nu),
+                 H1.ravel().copy(), range(H1.size))
+    assert max(np.abs(gW).max(), np.abs(gH).max()) < 1e-8
+    assert abs(trace[-1] - brute_loss(data, y, alpha, W1, H1, a0, lam, nu)) < 1e-10 * trace[-1]
