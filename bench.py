@@ -409,8 +409,6 @@ def run_ours(args):
         m2.close()
     if rank == 0 and args.foldin:
         line["foldin"] = run_foldin(cpu_sample=0 if args.no_cpu_baseline else 6)
-    if rank == 0 and args.subsample_error:
-        line["subsample_error"] = run_subsample_error(args, args.subsample_error)
     if rank == 0 and args.convergence:
         line["convergence"] = run_convergence(prob, args.convergence)
     if rank == 0 and args.autotune:
@@ -450,49 +448,6 @@ def run_convergence(prob, epochs):
             m.close()
         out[name] = res
     return out
-
-
-def subsample_problem(args):
-    """The workload at 1/100 of its users and positives (same distributions, all items):
-    the subsample on which the FP64 oracle checks the full-size configuration."""
-    from paper_2110_14044_gb300 import synth
-    cfg = synth.PRESETS[args.workload]
-    return synth.preset(args.workload, seed=0, n_users=max(1, cfg["n_users"] // 100),
-                        nnz=cfg["nnz"] // 100, **overrides(args))
-
-
-def run_subsample_error(args, epochs):
-    """Per-epoch error of the GPU path against the FP64 oracle on the 1% subsample."""
-    import oracle
-    import paper_2110_14044_gb300 as ials
-    from paper_2110_14044_gb300 import _abi
-    prob = subsample_problem(args)
-    prec = _abi.PREC_BF16 if args.precision == "bf16" else _abi.PREC_FP32
-    m = ials.Model(prob.data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu, precision=prec,
-                   graph=True, W0=prob.W0, H0=prob.H0)
-    P = oracle.Problem.from_data(prob.data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu)
-    t0 = time.perf_counter()
-    Wr, Hr, _, tr, st = oracle.ialspp(P, epochs, prob.W0, prob.H0, trace=True)
-    t_oracle = time.perf_counter() - t0
-    nb = prob.d // prob.b
-    rel = []
-    for e in range(epochs):
-        m.epoch(1)
-        ref = float(tr[(e + 1) * 2 * nb - 1])
-        rel.append(abs(m.objective() - ref) / abs(ref))
-    W, H = m.factors()
-
-    def emb(X, Xr):
-        n = np.linalg.norm(Xr, axis=1)
-        floor = max(1e-6 * float(np.median(n)), 1e-30)
-        return float(np.max(np.linalg.norm(X.astype(np.float64) - Xr, axis=1) / np.maximum(n, floor)))
-
-    m.close()
-    return {"desc": (f"1% subsample: {prob.data.n_users} users x {prob.data.n_items} items, "
-                     f"{prob.data.nnz} positives, d={prob.d}, b={prob.b}"),
-            "precision": args.precision, "epochs": epochs, "oracle_status": st,
-            "oracle_s": t_oracle, "rel_objective_error": rel,
-            "rel_embedding_error": {"W": emb(W, Wr), "H": emb(H, Hr)}}
 
 
 def run_ncu_step(args):
@@ -688,10 +643,6 @@ def main():
                     help="also time every admissible block size per precision (b sweep)")
     ap.add_argument("--convergence", type=int, default=0, metavar="E",
                     help="also record the objective over E epochs for every admissible b")
-    ap.add_argument("--subsample-error", type=int, default=0, metavar="E",
-                    help="also report the per-epoch error against the FP64 oracle on a 1%% "
-                         "user subsample of the workload, over E epochs (the oracle's FP64 "
-                         "Cholesky makes this slow at large b: minutes per epoch at d=1024, b=128)")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-step", action="store_true",
