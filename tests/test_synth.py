@@ -36,3 +36,21 @@ def test_zipf_user_activity_is_skewed_and_capped_at_the_catalogue():
     d2 = synth.make_interactions(n_users, n_items, nnz, 1.05, 0.0, 0.0, 5, 200_000, seed=4,
                                  user_zipf=1.3)
     np.testing.assert_array_equal(d.u_items, d2.u_items)
+
+
+def test_stored_oracle_trace_matches_the_generator():
+    """tests/golden/msd_subsample_trace.json was computed on the generator's 1% MSD-shaped
+    subsample; a change to the generator that alters those inputs must come with a new
+    trace (make_msd_subsample_trace.py), else the GPU comparison would only skip."""
+    import hashlib
+    import json
+    import os
+    rec = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "msd_subsample_trace.json")))
+    prob = synth.preset("msd_570k", seed=0, n_users=5700, nnz=340_000)
+    h = hashlib.sha256()
+    for a in (prob.data.u_indptr, prob.data.u_items, prob.W0, prob.H0):
+        h.update(np.ascontiguousarray(a).tobytes())
+    assert h.hexdigest()[:16] == rec["inputs_sha256_16"]
+    assert (prob.data.n_users, prob.data.n_items, prob.data.nnz, prob.d, prob.b) == (
+        rec["problem"]["n_users"], rec["problem"]["n_items"], rec["problem"]["nnz"],
+        rec["problem"]["d"], rec["problem"]["b"])
