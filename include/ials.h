@@ -196,7 +196,8 @@ ials_status ials_partial_gramian_bf16(const float *X, int64_t n, int32_t d, int3
  * The split-K partial sums live in one fixed device array of 2^21 floats
  * (8 MiB) that every GPU loading the library holds until the process exits;
  * calls with d * bs > 2^21 fail with IALS_EINVAL.  X (n x d) and G (d x bs)
- * are caller-owned device arrays.  Nothing is allocated or freed: no
+ * are caller-owned device (or managed) arrays; unlike the other calls, host
+ * arrays are not copied but refused with IALS_EINVAL.  Nothing is allocated or freed: no
  * cudaMalloc, cudaFree or allocating library routine is called.
  * The call only enqueues work on cuda_stream and returns; G is ready when the
  * stream reaches that point.  The first call on a device looks up the array's

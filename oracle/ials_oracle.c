@@ -240,51 +240,77 @@ typedef struct {
     int status;
 } half_ctx;
 
-/* The row update of Algorithm 3 for row r: gradient init, Hessian init, loop
- * over S_r, Newton step, apply, prediction-cache update.  When `apply` is 0
- * the new w_{r,pi} is written to out_w instead and nothing else changes. */
+/* The Newton system of one row's block (Eqs. 9, 11, 12).  The loss restricted
+ * to x_{r,pi} is quadratic, so its minimiser is one Newton step: with the
+ * (un-halved) gradient g and Hessian A of Eqs. 11-12, delta = A^-1 g and the
+ * block moves to x_{r,pi} - delta (Eq. 9).  Both statistics split into a part
+ * that involves every row of the fixed side only through the partial Gramian
+ * G^{pi} (Eq. 10) and a part summed over the row's own interactions S_r. */
+
+/* The Gramian part: g = alpha0 x_r G^{pi} + lambda_r x_{r,pi} (Eq. 11) and
+ * A = alpha0 G^{pi}_{pi} + lambda_r I (Eq. 12, "+ lambda" read as lambda_r I). */
+static void gramian_terms(const oracle_problem *P, int p0, int bs, const double *x,
+                          const double *G, double lam, double *A, double *g) {
+    const int d = P->d;
+    for (int f = 0; f < bs; ++f) {
+        double xg = 0.0;
+        for (int k = 0; k < d; ++k) xg += x[k] * G[k * bs + f];
+        g[f] = P->alpha0 * xg + lam * x[p0 + f];
+        for (int q = 0; q < bs; ++q)
+            A[f * bs + q] = P->alpha0 * G[(p0 + f) * bs + q] + (f == q ? lam : 0.0);
+    }
+}
+
+/* The observed part, added on: for every interaction (r, c) of S_r with weight
+ * alpha and label y, g += alpha (yhat - y) f_{c,pi} and A += alpha f_{c,pi}
+ * f_{c,pi}^T, where f_c is the fixed-side row of c (Eqs. 11-12).  On the item
+ * side the prediction of (u, i) is found through i_pos. */
+static void observed_terms(const oracle_problem *P, int side, int p0, int bs,
+                           const double *Fix, const double *yhat, int64_t r, double *A,
+                           double *g) {
+    const int d = P->d;
+    const int64_t *ptr = side == 0 ? P->u_ptr : P->i_ptr;
+    const int32_t *idx = side == 0 ? P->u_idx : P->i_idx;
+    for (int64_t s = ptr[r]; s < ptr[r + 1]; ++s) {
+        const int64_t q = side == 0 ? s : P->i_pos[s];
+        const double *f_c = Fix + (int64_t)idx[s] * d + p0;
+        const double a = av(P, q), res = a * (yhat[q] - yv(P, q));
+        for (int f = 0; f < bs; ++f) {
+            g[f] += res * f_c[f];
+            for (int t = 0; t < bs; ++t) A[f * bs + t] += a * f_c[f] * f_c[t];
+        }
+    }
+}
+
+/* Exact minimisation of L over x_{r,pi} (Eq. 8) by the Newton step of Eq. 9,
+ * as Algorithm 3 does for every row of a half-step.  With apply = 1 the row
+ * moves to x_{r,pi} - delta and every cached prediction of the row drops by
+ * <delta, f_{c,pi}> (the prediction is linear in x_r, Eq. 1); with apply = 0
+ * the new block goes to out_w and nothing changes.  A (bs x bs) and g (bs) are
+ * scratch. */
 static int row_update(const oracle_problem *P, int side, int p0, int bs, double *Upd,
                       const double *Fix, const double *G, double *yhat, int64_t r,
                       double *A, double *g, int apply, double *out_w) {
     const int d = P->d;
     const int64_t *ptr = side == 0 ? P->u_ptr : P->i_ptr;
     const int32_t *idx = side == 0 ? P->u_idx : P->i_idx;
-    double *w = Upd + r * d;
-    const int64_t n_r = ptr[r + 1] - ptr[r];
-    const double lam = P->lambda * (1.0 + P->nu * (double)n_r);
+    double *x = Upd + r * d;
+    const double lam = P->lambda * (1.0 + P->nu * (double)(ptr[r + 1] - ptr[r]));
 
-    /* grad <- alpha0 w G^{pi} + lambda w_pi ;  hess <- alpha0 G^{pi}_pi + lambda I */
-    for (int f = 0; f < bs; ++f) {
-        double t = 0.0;
-        for (int k = 0; k < d; ++k) t += w[k] * G[k * bs + f];
-        g[f] = P->alpha0 * t + lam * w[p0 + f];
-        for (int q = 0; q < bs; ++q)
-            A[f * bs + q] = P->alpha0 * G[(p0 + f) * bs + q] + (f == q ? lam : 0.0);
-    }
-    /* loop over (r, c, y, alpha) in S */
-    for (int64_t s = ptr[r]; s < ptr[r + 1]; ++s) {
-        const int64_t q = side == 0 ? s : P->i_pos[s];
-        const double *h = Fix + (int64_t)idx[s] * d + p0;
-        const double a = av(P, q), res = a * (yhat[q] - yv(P, q));
-        for (int f = 0; f < bs; ++f) {
-            g[f] += res * h[f];
-            for (int t = 0; t < bs; ++t) A[f * bs + t] += a * h[f] * h[t];
-        }
-    }
-    /* delta = hess^-1 grad */
-    if (cholesky_solve(A, g, bs)) return ORACLE_ENOTPD;
+    gramian_terms(P, p0, bs, x, G, lam, A, g);
+    observed_terms(P, side, p0, bs, Fix, yhat, r, A, g);
+    if (cholesky_solve(A, g, bs)) return ORACLE_ENOTPD; /* g now holds delta */
     if (!apply) {
-        for (int f = 0; f < bs; ++f) out_w[f] = w[p0 + f] - g[f];
+        for (int f = 0; f < bs; ++f) out_w[f] = x[p0 + f] - g[f];
         return ORACLE_OK;
     }
-    /* w_pi <- w_pi - delta ;  yhat <- yhat - <delta, h_pi> */
-    for (int f = 0; f < bs; ++f) w[p0 + f] -= g[f];
+    for (int f = 0; f < bs; ++f) x[p0 + f] -= g[f];
     for (int64_t s = ptr[r]; s < ptr[r + 1]; ++s) {
         const int64_t q = side == 0 ? s : P->i_pos[s];
-        const double *h = Fix + (int64_t)idx[s] * d + p0;
-        double t = 0.0;
-        for (int f = 0; f < bs; ++f) t += g[f] * h[f];
-        yhat[q] -= t;
+        const double *f_c = Fix + (int64_t)idx[s] * d + p0;
+        double change = 0.0;
+        for (int f = 0; f < bs; ++f) change += g[f] * f_c[f];
+        yhat[q] -= change;
     }
     return ORACLE_OK;
 }

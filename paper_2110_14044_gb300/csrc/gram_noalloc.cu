@@ -47,11 +47,28 @@ extern "C" ials_status ials_partial_gramian_noalloc(const float *X, int64_t n, i
                              std::to_string(kNoAllocScratchFloats) + " floats");
         return IALS_EINVAL;
     }
+    // X and G must be memory the GPU addresses directly: unlike the library's
+    // other calls this one copies nothing, so a host array is refused here
+    // rather than handed to the kernel.  cudaPointerGetAttributes allocates nothing.
+    for (const void *p : {static_cast<const void *>(X), static_cast<const void *>(G)}) {
+        cudaPointerAttributes at;
+        const cudaError_t pe = cudaPointerGetAttributes(&at, p);
+        if (pe != cudaSuccess) cudaGetLastError();
+        if (pe != cudaSuccess || (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            ials::set_last_error("X and G must be device (or managed) memory");
+            return IALS_EINVAL;
+        }
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (e != cudaSuccess) {
         ials::set_last_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
         cudaGetLastError();
+        return IALS_ECUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        ials::set_last_error("device index " + std::to_string(dev) + " exceeds the " +
+                             std::to_string(kMaxDevices) + " devices this entry point supports");
         return IALS_ECUDA;
     }
     float *ws = nullptr;

@@ -53,3 +53,39 @@ def test_noalloc_gramian_rejects_oversized_problem(abi):
         abi.ials_partial_gramian_noalloc(X, 4, 4096, 0, 1024, G)
     assert ei.value.status == abi.EINVAL
     assert "scratch" in abi.ials_last_error()
+
+
+def test_noalloc_gramian_rejects_host_arrays(abi):
+    import torch
+    n, d, bs = 64, 16, 8
+    Xh = np.ones((n, d), np.float32)
+    Gh = np.zeros((d, bs), np.float32)
+    Xd = torch.ones((n, d), dtype=torch.float32, device="cuda")
+    Gd = torch.zeros((d, bs), dtype=torch.float32, device="cuda")
+    for X, G in ((Xh, Gd), (Xd, Gh), (Xh, Gh)):
+        with pytest.raises(abi.IalsError) as ei:
+            abi.ials_partial_gramian_noalloc(X, n, d, 0, bs, G)
+        assert ei.value.status == abi.EINVAL
+        assert "device" in abi.ials_last_error()
+
+
+def test_noalloc_gramian_allocates_no_device_memory(abi):
+    """After the first call (which looks up the fixed array's address), further
+    calls leave both the driver's free-memory count and torch's allocator as they were."""
+    import torch
+    n, d, bs = 50000, 256, 64
+    X = torch.randn((n, d), dtype=torch.float32, device="cuda")
+    G = torch.empty((d, bs), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    abi.ials_partial_gramian_noalloc(X, n, d, 0, bs, G, stream)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    stats0 = torch.cuda.memory_stats()
+    for p0 in (0, 64, 128, 192):
+        abi.ials_partial_gramian_noalloc(X, n, d, p0, bs, G, stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    assert free1 == free0
+    for key in ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.current"):
+        assert stats1.get(key, 0) == stats0.get(key, 0), key
