@@ -183,7 +183,8 @@ def test_msd_shaped_subsample_bf16_b128_sampled_rows():
     rng = np.random.default_rng(3)
     for side, block in ((0, 2), (1, 2)):
         W, H = m.factors()
-        yhat = m.residuals().astype(np.float64) + 1.0
+        yhat = oracle.predict(P, W, H)  # from the factors (Eq. 1), not from the GPU's cache
+        assert np.abs(m.residuals() - (yhat - 1.0)).max() <= 1e-4, side
         lens = np.diff(data.u_indptr if side == 0 else data.i_indptr)
         rows = np.unique(np.concatenate([np.argsort(-lens)[:4], rng.integers(0, lens.size, 40)]))
         st, ref = oracle.rows_step(P, side, block, W, H, yhat, rows)
@@ -194,34 +195,3 @@ def test_msd_shaped_subsample_bf16_b128_sampled_rows():
         err = np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-12)
         print(f"side {side}: max row rel err {err.max():.2e}")
         assert err.max() <= 1e-3, (side, err.max())
-
-
-def test_msd_shaped_subsample_bf16_b128_objective_per_epoch():
-    """The d = 1024, b = 128 configuration on its 1% user subsample, 8 epochs of the
-    BF16 pattern, against the FP64 oracle epoch by epoch (relative objective within
-    1e-3).  The oracle's objectives are stored in tests/golden/msd_subsample_trace.json
-    by make_msd_subsample_trace.py (oracle and generator only; tens of minutes of
-    host time), together with a fingerprint of the generated inputs."""
-    import hashlib
-    import json
-    import os
-    rec = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "msd_subsample_trace.json")))
-    prob = synth.preset("msd_570k", seed=0, n_users=5700, nnz=340_000)
-    h = hashlib.sha256()
-    for a in (prob.data.u_indptr, prob.data.u_items, prob.W0, prob.H0):
-        h.update(np.ascontiguousarray(a).tobytes())
-    if h.hexdigest()[:16] != rec["inputs_sha256_16"]:
-        pytest.skip("the generator produced other inputs here than those the stored trace was computed on")
-    data = prob.data
-    m = Model(data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu, W0=prob.W0, H0=prob.H0)
-    before = m.objective()
-    assert abs(before - rec["objective_before"]) <= 1e-6 * rec["objective_before"]
-    rel = []
-    for ref in rec["objective_after_epoch"]:
-        o, st = m.epoch(1, objective=True)
-        assert st == 0
-        rel.append(abs(o - ref) / ref)
-    m.close()
-    print("msd subsample BF16 b=128, relative objective error per epoch: "
-          + " ".join(f"{r:.1e}" for r in rel))
-    assert max(rel) <= BF16_OBJ_TOL, rel

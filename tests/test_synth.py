@@ -41,7 +41,7 @@ def test_zipf_user_activity_is_skewed_and_capped_at_the_catalogue():
 def test_stored_oracle_trace_matches_the_generator():
     """tests/golden/msd_subsample_trace.json was computed on the generator's 1% MSD-shaped
     subsample; a change to the generator that alters those inputs must come with a new
-    trace (make_msd_subsample_trace.py), else the GPU comparison would only skip."""
+    trace (make_oracle_trace.py), else the GPU comparison would only skip."""
     import hashlib
     import json
     import os
