@@ -121,6 +121,49 @@ def job_throughput(units_per_rank, world, ms_max):
     return world * units_per_rank / (ms_max / 1e3)
 
 
+# ----------------------------------------------------------------- error against stored oracle traces
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def inputs_fingerprint(data, W0, H0):
+    """sha256 (first 16 hex) of the inputs a stored oracle trace was computed on."""
+    import hashlib
+    h = hashlib.sha256()
+    for a in (data.u_indptr, data.u_items, W0, H0):
+        h.update(np.ascontiguousarray(a).tobytes())
+    return h.hexdigest()[:16]
+
+
+def load_trace(name):
+    try:
+        return json.load(open(os.path.join(GOLDEN, name)))
+    except OSError:
+        return None
+
+
+def trace_errors(data, d, b, alpha0, lam, nu, W0, H0, precision, trace_name, stream=None):
+    """Relative objective error per epoch of a fresh CUDA-graph run from (W0, H0)
+    against the FP64 oracle's stored trace (written by tests/golden/make_oracle_trace.py,
+    oracle and generator only), or the reason there is none."""
+    import paper_2110_14044_gb300 as ials
+    rec = load_trace(trace_name)
+    if rec is None:
+        return {"trace": trace_name, "missing": True}
+    pr = rec["problem"]
+    if (pr["d"], pr["b"], pr["n_users"], pr["nnz"]) != (d, b, data.n_users, int(data.u_indptr[-1])) or \
+            inputs_fingerprint(data, W0, H0) != rec["inputs_sha256_16"]:
+        return {"trace": trace_name, "skipped": "inputs differ from those the trace was computed on"}
+    m = ials.Model(data, d, b, alpha0, lam, nu, precision=precision, graph=True, stream=stream,
+                   W0=W0, H0=H0)
+    rel = []
+    for ref in rec["objective_after_epoch"]:
+        o, _ = m.epoch(1, objective=True)
+        rel.append(abs(o - ref) / abs(ref))
+    m.close()
+    return {"trace": trace_name, "epochs": len(rel), "rel_objective_error_per_epoch": rel,
+            "max": max(rel) if rel else None}
+
+
 def launches_per_epoch(kern, steps, bf16, b):
     """Kernel launches per epoch from the profiled intervals ({kind: (ms, marks)}).
 
@@ -258,10 +301,60 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def kernel_rooflines(m, steps, prec, b, precision_name, workload_key, peaks):
+    """Per-kernel-kind device time over `steps` eager epochs (CUDA events around every
+    launch, on the context's stream) against the algorithmic work of the context's own
+    decomposition: the dominant kernel's `roofline` and every kind's fractions."""
+    from paper_2110_14044_gb300 import _abi
+    kern, prof_total, _ = _abi.ials_profile_epochs(m.ctx, steps)
+    work = _abi.ials_work_model(m.ctx)
+    n_launch_epoch = launches_per_epoch(kern, steps, prec == _abi.PREC_BF16, b)
+    dom = max(("sparse", "gram", "rowterm", "residual", "split_solve", "split_resid"),
+              key=lambda k: kern[k][0])
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    dms, dcnt = kern[dom]
+    dbytes = work[dom][0] * steps  # bytes over all profiled launches
+    achieved = dbytes / (dms / 1e3) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": measured_traffic(dom, precision_name, workload_key),
+                "peak_source": peak_src,
+                "bytes_per_launch": dbytes / max(dcnt, 1), "ms_per_launch": dms / max(dcnt, 1),
+                "gflops": work[dom][1] * steps / (dms / 1e3) / 1e9}
+    # every kernel kind against its own roofline: algorithmic bytes / event time against the
+    # measured copy bandwidth; FLOPs against the tensor peak (BF16 tensor-core kernels: the
+    # measured burst bf16 peak) or the FP32 FMA peak (152 SMs x 128 FMA x 2 x max SM clock)
+    fma_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    tensor_kinds = ("gram", "rowterm", "sparse") if prec == _abi.PREC_BF16 else ()
+    per_kind = {}
+    for k, (kms, kcnt) in kern.items():
+        if kms <= 0 or k == "objective":
+            continue
+        gbs = work[k][0] * steps / (kms / 1e3) / 1e9
+        tfs = work[k][1] * steps / (kms / 1e3) / 1e12
+        fpk = peaks.get("bf16_tflops", 1900.0) if k in tensor_kinds else fma_peak
+        per_kind[k] = {"ms_per_epoch": kms / steps, "GB/s": gbs, "hbm_frac": gbs / hbm_peak,
+                       "TFLOP/s": tfs, "flop_peak": fpk, "flop_frac": tfs / fpk}
+    return roofline, per_kind, kern, prof_total, n_launch_epoch
+
+
 # ----------------------------------------------------------------- our arm
 def run_ours(args):
-    import torch
     rank, local_rank, world = env_rank()
+    msd_job = None
+    if rank == 0 and args.d1024 and args.workload == WORKLOAD and not (args.d or args.b):
+        # the d = 1024 workload's interaction set is drawn in a spawned process (no CUDA
+        # in it) while the d = 128 measurements run
+        msd_job = start_msd_generation()
+    import torch
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -307,40 +400,9 @@ def run_ours(args):
     value = job_throughput(rows_per_epoch * args.steps, world, ms)
 
     # per-kernel device times over the same number of eager epochs (events per launch)
-    kern, prof_total, _ = _abi.ials_profile_epochs(m.ctx, args.steps)
-    work = _abi.ials_work_model(m.ctx)
-    n_launch_epoch = launches_per_epoch(kern, args.steps, prec == _abi.PREC_BF16, prob.b)
-    dom = max(("sparse", "gram", "rowterm", "residual", "split_solve", "split_resid"),
-              key=lambda k: kern[k][0])
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    dms, dcnt = kern[dom]
-    dbytes = work[dom][0] * args.steps  # bytes over all profiled launches
-    achieved = dbytes / (dms / 1e3) / 1e9
-    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": measured_traffic(dom, args.precision, (args.workload, prob.d, prob.b)),
-                "peak_source": peak_src,
-                "bytes_per_launch": dbytes / max(dcnt, 1), "ms_per_launch": dms / max(dcnt, 1),
-                "gflops": work[dom][1] * args.steps / (dms / 1e3) / 1e9}
-    # every kernel kind against its own roofline: algorithmic bytes / event time against the
-    # measured copy bandwidth; FLOPs against the tensor peak (BF16 tensor-core kernels: the
-    # measured burst bf16 peak) or the FP32 FMA peak (152 SMs x 128 FMA x 2 x max SM clock)
-    fma_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    tensor_kinds = ("gram", "rowterm", "sparse") if prec == _abi.PREC_BF16 else ()
-    per_kind = {}
-    for k, (kms, kcnt) in kern.items():
-        if kms <= 0 or k == "objective":
-            continue
-        gbs = work[k][0] * args.steps / (kms / 1e3) / 1e9
-        tfs = work[k][1] * args.steps / (kms / 1e3) / 1e12
-        fpk = peaks.get("bf16_tflops", 1900.0) if k in tensor_kinds else fma_peak
-        per_kind[k] = {"ms_per_epoch": kms / args.steps, "GB/s": gbs, "hbm_frac": gbs / hbm_peak,
-                       "TFLOP/s": tfs, "flop_peak": fpk, "flop_frac": tfs / fpk}
+    peaks = load_peaks()
+    roofline, per_kind, kern, prof_total, n_launch_epoch = kernel_rooflines(
+        m, args.steps, prec, prob.b, args.precision, (args.workload, prob.d, prob.b), peaks)
 
     # end to end through the public API: factors in from pinned host memory,
     # one epoch, factors back to pinned host memory, every step
@@ -400,13 +462,26 @@ def run_ours(args):
         ev1.record(stream)
         barrier()
         ms2 = ev0.elapsed_time(ev1) / args.steps
+        o_after2 = m2.objective()
+        roof2, kinds2, _, _, _ = kernel_rooflines(m2, args.steps, oprec, prob.b, other,
+                                                  (args.workload, prob.d, prob.b), peaks)
         line["variants"] = {
             args.precision: {"epoch_s": ms_per_step / 1e3, "rows_per_s": value / world,
                              "objective_after": obj_after},
             other: {"epoch_s": ms2 / 1e3, "rows_per_s": rows_per_epoch / (ms2 / 1e3),
-                    "objective_before": o0, "objective_after": m2.objective()},
+                    "objective_before": o0, "objective_after": o_after2,
+                    "roofline": roof2, "kernels_roofline": kinds2},
         }
         m2.close()
+    if rank == 0 and args.workload == WORKLOAD and not (args.d or args.b):
+        # error of every precision against the FP64 oracle, epoch by epoch, from the same
+        # initial factors as the oracle's stored 16-epoch trace of this workload
+        line["error_vs_oracle"] = {
+            name: trace_errors(data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu, prob.W0, prob.H0,
+                               pr, "ml20m_trace.json", stream)
+            for name, pr in (("fp32", _abi.PREC_FP32), ("bf16", _abi.PREC_BF16))}
+    if msd_job is not None:
+        line["d1024"] = run_msd(msd_job, args, stream, peaks)
     if rank == 0 and args.foldin:
         line["foldin"] = run_foldin(cpu_sample=0 if args.no_cpu_baseline else 6)
     if rank == 0 and args.convergence:
@@ -424,6 +499,99 @@ def run_ours(args):
     m.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# ----------------------------------------------------------------- the d = 1024 workload
+MSD = "msd_570k"
+MSD_BLOCKS = (32, 64, 128)   # the autotuner's candidates at d = 1024 (b = 128 is the stated one)
+
+
+def _draw_msd(out_dir):
+    """Child process: draw the MSD-shaped interaction set and save its CSR views."""
+    from paper_2110_14044_gb300 import synth
+    c = synth.PRESETS[MSD]
+    data = synth.make_interactions(c["n_users"], c["n_items"], c["nnz"], c["zipf_s"], c["ln_mu"],
+                                   c["ln_sigma"], c["len_min"], c["len_max"], 0)
+    for k in ("u_indptr", "u_items", "i_indptr", "i_users"):
+        np.save(os.path.join(out_dir, k + ".npy"), getattr(data, k))
+
+
+def start_msd_generation():
+    import multiprocessing as mp
+    out_dir = tempfile.mkdtemp(prefix="msd_")
+    proc = mp.get_context("spawn").Process(target=_draw_msd, args=(out_dir,))
+    proc.start()
+    return proc, out_dir
+
+
+def run_msd(job, args, stream, peaks):
+    """The metric's d = 1024 half: the MSD-shaped workload (570,000 x 41,000, 34M
+    positives, d = 1024), FP32 and BF16 side by side at the stated b = 128 and at every
+    autotuner candidate (the fastest is the autotuned b), with the rooflines of the
+    stated and autotuned configurations and the per-epoch error against the FP64
+    oracle on the 1% user subsample (stored traces; b = 128 and b = 32)."""
+    import shutil
+    import torch
+    import paper_2110_14044_gb300 as ials
+    from paper_2110_14044_gb300 import _abi, autotune, synth
+    proc, out_dir = job
+    proc.join()
+    if proc.exitcode != 0:
+        return {"error": f"generator process exited with {proc.exitcode}"}
+    arrs = {k: np.load(os.path.join(out_dir, k + ".npy")) for k in ("u_indptr", "u_items", "i_indptr", "i_users")}
+    shutil.rmtree(out_dir, ignore_errors=True)
+    c = synth.PRESETS[MSD]
+    data = synth.Interactions(c["n_users"], c["n_items"], **arrs)
+    d = c["d"]
+    rows_plain = data.n_users + data.n_items
+    out = {"workload": WORKLOADS[MSD], "initial_factors": "the library's seeded N(0, (0.1/sqrt(d))^2) draw",
+           "steps": args.d1024_steps, "warmup": 1, "stated_b": c["b"], "configs": {}}
+    K = max(1, args.d1024_steps)
+    best = {}
+    for pname, prec in (("bf16", _abi.PREC_BF16), ("fp32", _abi.PREC_FP32)):
+        for b in MSD_BLOCKS:
+            if not autotune.admissible(d, b, prec):
+                continue
+            m = ials.Model(data, d, b, c["alpha0"], c["lam"], c["nu"], precision=prec, graph=True,
+                           stream=stream)
+            m.epoch(1)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            _, st = m.epoch(K)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / K
+            rec = {"precision": pname, "b": b, "epoch_s": ms / 1e3,
+                   "rows_per_s": rows_plain * (d // b) / (ms / 1e3), "rows_per_s_plain": rows_plain / (ms / 1e3),
+                   "objective_after": m.objective(), "status": st}
+            if b == c["b"]:
+                rec["roofline"], rec["kernels_roofline"], _, _, _ = kernel_rooflines(
+                    m, 1, prec, b, pname, (MSD, d, b), peaks)
+            out["configs"][f"{pname}_b{b}"] = rec
+            if pname not in best or ms < out["configs"][f"{pname}_b{best[pname]}"]["epoch_s"] * 1e3:
+                best[pname] = b
+            m.close()
+    out["autotuned_b"] = best
+    for pname, b in best.items():
+        key = f"{pname}_b{b}"
+        if "roofline" not in out["configs"][key]:
+            prec = _abi.PREC_BF16 if pname == "bf16" else _abi.PREC_FP32
+            m = ials.Model(data, d, b, c["alpha0"], c["lam"], c["nu"], precision=prec, stream=stream)
+            m.epoch(1)
+            out["configs"][key]["roofline"], out["configs"][key]["kernels_roofline"], _, _, _ = \
+                kernel_rooflines(m, 1, prec, b, pname, (MSD, d, b), peaks)
+            m.close()
+    # error against the FP64 oracle on the 1% user subsample, epoch by epoch
+    err = {"sample": "1% user subsample of the same generator: 5,700 users x 41,000 items, "
+                     "340,000 positives, d = 1024, seeded W0/H0; FP64 oracle traces stored in tests/golden"}
+    for b, tname in ((128, "msd_subsample_trace.json"), (32, "msd_subsample_b32_trace.json")):
+        sub = synth.preset(MSD, seed=0, n_users=c["n_users"] // 100, nnz=c["nnz"] // 100, b=b)
+        for pname, prec in (("fp32", _abi.PREC_FP32), ("bf16", _abi.PREC_BF16)):
+            err[f"{pname}_b{b}"] = trace_errors(sub.data, d, b, sub.alpha0, sub.lam, sub.nu, sub.W0, sub.H0,
+                                                prec, tname, stream)
+    out["error_vs_oracle"] = err
+    return out
 
 
 def run_convergence(prob, epochs):
@@ -643,6 +811,10 @@ def main():
                     help="also time every admissible block size per precision (b sweep)")
     ap.add_argument("--convergence", type=int, default=0, metavar="E",
                     help="also record the objective over E epochs for every admissible b")
+    ap.add_argument("--no-d1024", dest="d1024", action="store_false",
+                    help="do not also measure the MSD-shaped d = 1024 workload")
+    ap.add_argument("--d1024-steps", type=int, default=3,
+                    help="timed epochs per configuration of the d = 1024 workload")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-step", action="store_true",

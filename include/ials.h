@@ -68,7 +68,10 @@ enum {
 /* ials_params.flags */
 enum {
     IALS_FLAG_GRAPH = 1,      /* capture one epoch as a CUDA graph and replay it */
-    IALS_FLAG_FORCE_FP64 = 2  /* fault injection: treat every FP32 pivot as failed */
+    IALS_FLAG_FORCE_FP64 = 2, /* fault injection: treat every FP32 pivot as failed */
+    IALS_FLAG_GENERAL = 4     /* run the general block path also at the end points b = 1
+                               * (otherwise iCD, Algorithm 2) and b = d (otherwise iALS,
+                               * Algorithm 1) */
 };
 
 typedef struct {

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libials.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTPD, EAGAIN, ETIMEDOUT, ENOTFOUND = range(8)
 PREC_FP32, PREC_BF16 = 0, 1
-FLAG_GRAPH, FLAG_FORCE_FP64 = 1, 2
+FLAG_GRAPH, FLAG_FORCE_FP64, FLAG_GENERAL = 1, 2, 4
 
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTPD", 5: "EAGAIN",
            6: "ETIMEDOUT", 7: "ENOTFOUND"}

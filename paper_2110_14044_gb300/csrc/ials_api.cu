@@ -142,6 +142,9 @@ struct ials_ctx {
     double *obj_part = nullptr;
     int32_t n_obj_part = 0;
     double *g64a = nullptr, *g64b = nullptr, *g64ws = nullptr;
+    // iCD path (b = 1): Gramian columns (two of d), their partials, completion counter
+    float *icd_g = nullptr, *icd_gpart = nullptr;
+    int32_t *icd_done = nullptr;
     cudaGraphExec_t graph = nullptr;
     bool own_stream = false;
     bool e_stale = false;  // W or H replaced since the residual cache was last computed
@@ -250,7 +253,128 @@ cudaError_t launch_sparse_bf16(int32_t b, const StepArgs &a, cudaStream_t s) {
     }
 }
 
+// Arguments of one block-side step on the context's buffers.
+StepArgs step_args(ials_ctx *c, int side, int p0, Profiler *prof) {
+    SideDev &sd = c->side[side];
+    StepArgs a{};
+    a.ptr = sd.ptr;
+    a.idx = sd.idx;
+    a.pos = side == 1 ? sd.pos : nullptr;
+    a.e = c->e;
+    a.alpha = c->alpha;
+    a.y = c->y;
+    a.X = side == 0 ? c->W : c->H;
+    a.F = side == 0 ? c->H : c->W;
+    a.G = c->G;
+    a.R = c->R;
+    a.n_rows = sd.n_rows;
+    a.d = c->p.d;
+    a.b = c->p.b;
+    a.p0 = p0;
+    a.alpha0 = (float)c->p.alpha0;
+    a.lambda = (float)c->p.lambda;
+    a.nu = (float)c->p.nu;
+    a.tasks = sd.tasks;
+    a.n_tasks = sd.n_tasks;
+    a.split = sd.split;
+    a.n_split = sd.n_split;
+    a.stasks = sd.stasks;
+    a.n_stasks = sd.n_stasks;
+    a.part = c->part;
+    a.delta = c->delta;
+    a.counter = c->ctl;
+    a.retry = c->ctl + 1;
+    a.stats = c->stats;
+    a.force_fp64 = (c->p.flags & IALS_FLAG_FORCE_FP64) ? 1 : 0;
+    a.prof = prof;
+    a.Xh = side == 0 ? c->Wh : c->Hh;
+    a.Xl = side == 0 ? c->Wl : c->Hl;
+    a.Fh = side == 0 ? c->Hh : c->Wh;
+    a.Fl = side == 0 ? c->Hl : c->Wl;
+    return a;
+}
+
+// The iCD path (Algorithm 2) runs for b = 1 unless the general path is forced.
+bool use_icd(const ials_ctx *c) { return c->p.b == 1 && !(c->p.flags & IALS_FLAG_GENERAL); }
+
+// One iCD pass: side `side`, coordinate f, fixed-side Gramian column in g_in;
+// forms the updated side's column fn (>= 0) into g_out on the way.
+ials_status icd_pass_enqueue(ials_ctx *c, int side, int f, int fn, const float *g_in, float *g_out,
+                             Profiler *prof) {
+    IcdArgs a;
+    a.s = step_args(c, side, f, prof);
+    a.f = f;
+    a.fn = fn;
+    a.g_in = g_in;
+    a.g_out = g_out;
+    a.gpart = c->icd_gpart;
+    a.done = c->icd_done;
+    a.grid = icd_row_grid(a.s.n_tasks, c->p.d);
+    IALS_CUDA(launch_icd(a, c->stream), "iCD pass");
+    return IALS_OK;
+}
+
+// The iALS path (Algorithm 1) runs for b = d in {64, 128} unless the general path is forced.
+bool use_ials(const ials_ctx *c) {
+    return c->p.b == c->p.d && (c->p.b == 64 || c->p.b == 128) && !(c->p.flags & IALS_FLAG_GENERAL);
+}
+
+// One iALS epoch (Algorithm 1): per side the full Gramian G of the fixed side,
+// then every row solved directly from Eq. 3 (statistics sum alpha f f^T and
+// sum alpha y f, dense terms alpha0 G + lambda_r I).  No residual cache is
+// read or kept.
+ials_status direct_epoch_enqueue(ials_ctx *c, Profiler *prof) {
+    const int32_t d = c->p.d;
+    cudaStream_t s = c->stream;
+    for (int side = 0; side < 2; ++side) {
+        const int64_t n_fixed = side == 0 ? c->n_items : c->n_users;
+        prof_mark(prof, K_GRAM, s);
+        if (c->p.precision == IALS_PREC_BF16) {
+            IALS_CUDA(launch_gram_tc(c->maps[side == 0 ? 1 : 0], n_fixed, d, 0, d, c->G, c->gram_ws, c->dev_err, s),
+                      "Gramian (tcgen05)");
+        } else {
+            IALS_CUDA(launch_gram(side == 0 ? c->H : c->W, n_fixed, d, 0, d, c->G, c->gram_ws, s), "Gramian");
+        }
+        prof_mark(prof, -1, s);
+        IALS_CUDA(cudaMemsetAsync(c->ctl, 0, 2 * sizeof(int32_t), s), "counter reset");
+        StepArgs a = step_args(c, side, 0, prof);
+        a.direct = 1;
+        if (c->p.precision == IALS_PREC_BF16) {
+            IALS_CUDA(launch_sparse_bf16(d, a, s), "iALS row solves (BF16)");
+        } else {
+            IALS_CUDA(launch_sparse(a, s), "iALS row solves");
+        }
+    }
+    return IALS_OK;
+}
+
+// One iCD epoch: for every coordinate f the user pass, then the item pass
+// (Algorithm 2).  H's column 0 is formed once; every later column comes out of
+// the pass before the one that needs it.
+ials_status icd_epoch_enqueue(ials_ctx *c, Profiler *prof) {
+    const int d = c->p.d;
+    float *gH = c->icd_g, *gW = c->icd_g + d;
+    prof_mark(prof, K_GRAM, c->stream);
+    IALS_CUDA(launch_gram(c->H, c->n_items, d, 0, 1, gH, c->gram_ws, c->stream), "Gramian column");
+    prof_mark(prof, -1, c->stream);
+    for (int f = 0; f < d; ++f) {
+        ials_status st = icd_pass_enqueue(c, 0, f, f, gH, gW, prof);
+        if (st != IALS_OK) return st;
+        st = icd_pass_enqueue(c, 1, f, f + 1 < d ? f + 1 : -1, gW, gH, prof);
+        if (st != IALS_OK) return st;
+    }
+    return IALS_OK;
+}
+
 ials_status step_enqueue(ials_ctx *c, int side, int block, Profiler *prof = nullptr) {
+    if (use_icd(c)) {  // one coordinate: its Gramian column of the fixed side, then the pass
+        const float *F = side == 0 ? c->H : c->W;
+        const int64_t n_fixed = side == 0 ? c->n_items : c->n_users;
+        prof_mark(prof, K_GRAM, c->stream);
+        IALS_CUDA(launch_gram(F, n_fixed, c->p.d, block, 1, c->icd_g, c->gram_ws, c->stream), "Gramian column");
+        prof_mark(prof, -1, c->stream);
+        return icd_pass_enqueue(c, side, block, -1, c->icd_g, nullptr, prof);
+    }
     const int32_t d = c->p.d, b = c->p.b, p0 = block * b;
     SideDev &sd = c->side[side];
     float *X = side == 0 ? c->W : c->H;
@@ -276,40 +400,7 @@ ials_status step_enqueue(ials_ctx *c, int side, int block, Profiler *prof = null
     }
     prof_mark(prof, -1, s);
     IALS_CUDA(cudaMemsetAsync(c->ctl, 0, 2 * sizeof(int32_t), s), "counter reset");
-    StepArgs a;
-    a.ptr = sd.ptr;
-    a.idx = sd.idx;
-    a.pos = side == 1 ? sd.pos : nullptr;
-    a.e = c->e;
-    a.alpha = c->alpha;
-    a.X = X;
-    a.F = F;
-    a.G = c->G;
-    a.R = c->R;
-    a.n_rows = sd.n_rows;
-    a.d = d;
-    a.b = b;
-    a.p0 = p0;
-    a.alpha0 = (float)c->p.alpha0;
-    a.lambda = (float)c->p.lambda;
-    a.nu = (float)c->p.nu;
-    a.tasks = sd.tasks;
-    a.n_tasks = sd.n_tasks;
-    a.split = sd.split;
-    a.n_split = sd.n_split;
-    a.stasks = sd.stasks;
-    a.n_stasks = sd.n_stasks;
-    a.part = c->part;
-    a.delta = c->delta;
-    a.counter = c->ctl;
-    a.retry = c->ctl + 1;
-    a.stats = c->stats;
-    a.force_fp64 = (c->p.flags & IALS_FLAG_FORCE_FP64) ? 1 : 0;
-    a.prof = prof;
-    a.Xh = side == 0 ? c->Wh : c->Hh;
-    a.Xl = side == 0 ? c->Wl : c->Hl;
-    a.Fh = side == 0 ? c->Hh : c->Wh;
-    a.Fl = side == 0 ? c->Hl : c->Wl;
+    StepArgs a = step_args(c, side, p0, prof);
     if (c->p.precision == IALS_PREC_BF16) {
         IALS_CUDA(launch_sparse_bf16(b, a, s), "sparse block step (BF16)");
     } else {
@@ -319,9 +410,11 @@ ials_status step_enqueue(ials_ctx *c, int side, int block, Profiler *prof = null
 }
 
 ials_status epoch_enqueue(ials_ctx *c, Profiler *prof = nullptr) {
+    if (use_ials(c)) return direct_epoch_enqueue(c, prof);
     prof_mark(prof, K_RESIDUAL, c->stream);
     IALS_CUDA(residual_enqueue(c), "residual recompute");
     prof_mark(prof, -1, c->stream);
+    if (use_icd(c)) return icd_epoch_enqueue(c, prof);
     const int nb = c->p.d / c->p.b;
     for (int k = 0; k < nb; ++k)
         for (int side = 0; side < 2; ++side) {
@@ -543,6 +636,13 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     ALLOC(c->obj, 3, "objective");
     c->n_obj_part = 4 * 152;
     ALLOC(c->obj_part, c->n_obj_part, "objective partials");
+    if (b == 1) {
+        ALLOC(c->icd_g, 2 * (int64_t)d, "Gramian columns");
+        ALLOC(c->icd_gpart, (int64_t)(icd_row_grid(std::max(c->side[0].n_tasks, c->side[1].n_tasks), d) +
+                                      icd_split_grid(max_split)) * d,
+              "Gramian column partials");
+        ALLOC(c->icd_done, 1, "completion counter");
+    }
     ALLOC(c->g64a, (int64_t)d * d, "FP64 Gramian");
     ALLOC(c->g64b, (int64_t)d * d, "FP64 Gramian");
     ALLOC(c->g64ws, std::max(gram64_ws_doubles(n_users, d), gram64_ws_doubles(n_items, d)),
@@ -572,6 +672,7 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     if (e3 == cudaSuccess && c->Wh) e3 = launch_split_bf16(c->W, (int64_t)n_users * d, c->Wh, c->Wl, c->stream);
     if (e3 == cudaSuccess && c->Hh) e3 = launch_split_bf16(c->H, (int64_t)n_items * d, c->Hh, c->Hl, c->stream);
     if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->dev_err, 0, sizeof(int32_t), c->stream);
+    if (e3 == cudaSuccess && c->icd_done) e3 = cudaMemsetAsync(c->icd_done, 0, sizeof(int32_t), c->stream);
     if (e3 == cudaSuccess && c->Wh &&
         (!make_gram_maps(c->maps[0], c->Wh, c->Wl, n_users, d, b) ||
          !make_gram_maps(c->maps[1], c->Hh, c->Hl, n_items, d, b) ||
@@ -586,26 +687,12 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     // Set kernel attributes of both sides' sparse variants now, outside any
     // stream capture: an empty step launches nothing but the (idle) retry kernel.
     cudaError_t e7 = cudaSuccess;
-    for (int sd = 0; sd < 2 && e7 == cudaSuccess; ++sd) {
-        StepArgs a{};
-        a.ptr = c->side[sd].ptr;
-        a.idx = c->side[sd].idx;
-        a.pos = sd == 1 ? c->side[1].pos : nullptr;
-        a.e = c->e;
-        a.alpha = c->alpha;
-        a.X = sd == 0 ? c->W : c->H;
-        a.F = sd == 0 ? c->H : c->W;
-        a.G = c->G;
-        a.R = c->R;
-        a.d = d;
-        a.b = b;
-        a.counter = c->ctl;
-        a.retry = c->ctl + 1;
-        a.stats = c->stats;
-        a.Xh = sd == 0 ? c->Wh : c->Hh;
-        a.Xl = sd == 0 ? c->Wl : c->Hl;
-        a.Fh = sd == 0 ? c->Hh : c->Wh;
-        a.Fl = sd == 0 ? c->Hl : c->Wl;
+    for (int k = 0; k < (use_ials(c) ? 4 : 2) && e7 == cudaSuccess; ++k) {
+        const int sd = k & 1;
+        StepArgs a = step_args(c, sd, 0, nullptr);
+        a.n_tasks = a.n_split = a.n_stasks = 0;
+        a.n_rows = 0;
+        a.direct = k >> 1;  // the iALS path's variants too
         e7 = cudaMemsetAsync(c->ctl, 0, 2 * sizeof(int32_t), c->stream);
         if (e7 == cudaSuccess) {
             if (p.precision == IALS_PREC_BF16)
@@ -614,6 +701,7 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
                 e7 = launch_sparse(a, c->stream);
         }
     }
+    if (e7 == cudaSuccess && b == 1) e7 = icd_prepare();
     cudaError_t e8 = cudaStreamSynchronize(c->stream);
     for (cudaError_t e : {e1, e2, e3, e4, e5, e6, e7, e8})
         if (e != cudaSuccess) { delete c; return cuda_fail(e, "context initialisation"); }
@@ -650,7 +738,8 @@ ials_status ials_epoch(ials_ctx *c, int32_t n_epochs, double *objective_after) {
             if (st != IALS_OK) return st;
         }
     }
-    if (n_epochs > 0) c->e_stale = false;  // each epoch recomputed the cache first
+    // each epoch recomputed the cache first; the iALS path keeps none
+    if (n_epochs > 0) c->e_stale = use_ials(c);
     ials_status st = finish(c);
     if (objective_after && (st == IALS_OK || st == IALS_ENOTPD)) {
         ials_status s2 = objective_enqueue(c);
@@ -740,7 +829,7 @@ ials_status ials_profile_epochs(ials_ctx *c, int32_t n_epochs, double *kernel_ms
         ials_status st = epoch_enqueue(c, &prof);
         if (st != IALS_OK) return st;
     }
-    if (n_epochs > 0) c->e_stale = false;
+    if (n_epochs > 0) c->e_stale = use_ials(c);
     prof_mark(&prof, -1, c->stream);
     ials_status st = finish(c);
     if (st != IALS_OK && st != IALS_ENOTPD) return st;

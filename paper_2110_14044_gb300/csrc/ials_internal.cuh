@@ -39,6 +39,16 @@ inline void prof_mark(Profiler *p, int k, cudaStream_t s) {
 }
 
 #ifdef __CUDACC__
+// x = v for one coordinate, keeping the BF16 hi/lo shadow current (BF16 mode).
+__device__ __forceinline__ void set_value(float *X, __nv_bfloat16 *Xh, __nv_bfloat16 *Xl, int64_t i, float v) {
+    X[i] = v;
+    if (Xh) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        Xh[i] = h;
+        Xl[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
 // x -= delta for one coordinate, keeping the BF16 hi/lo shadow current (BF16 mode).
 __device__ __forceinline__ void apply_delta(float *X, __nv_bfloat16 *Xh, __nv_bfloat16 *Xl,
                                             int64_t i, float delta) {
@@ -81,6 +91,7 @@ struct StepArgs {
     const int32_t *pos;     // side 1: CSR position -> user-major residual index; nullptr on side 0
     float *e;               // residual cache r = yhat - y, user-major order
     const float *alpha;     // per interaction weights (user-major) or nullptr
+    const float *y;         // per interaction labels (user-major) or nullptr (all ones)
     float *X;               // updated side, n_rows x d
     const float *F;         // fixed side, n_fixed x d
     // BF16 mode: hi/lo shadows (x = hi + lo to ~16 bits) of the updated and fixed sides;
@@ -104,8 +115,27 @@ struct StepArgs {
     int32_t *retry;         // [0] = count, [1..] = rows to redo in FP64
     int64_t *stats;         // [0] = FP64 retries, [1] = not positive definite
     int32_t force_fp64;     // fault injection: every FP32 pivot counts as failed
+    int32_t direct;         // b = d (Algorithm 1): solve for x_r itself from sum alpha y f, no residuals
     Profiler *prof;         // host only: event marks around launches, or nullptr
 };
+
+// One iCD pass (b = 1, Algorithm 2) over one side for coordinate f
+// (k_icd.cu).  part holds two floats per chunk slot, delta one per long row.
+struct IcdArgs {
+    StepArgs s;
+    int32_t f;           // coordinate updated by the pass
+    int32_t fn;          // column of the updated side's Gramian formed on the way (-1: none)
+    const float *g_in;   // column f of the fixed side's Gramian (d floats)
+    float *g_out;        // column fn of the updated side's Gramian after the pass (d floats)
+    float *gpart;        // partial columns: icd_row_grid blocks, then icd_split_grid blocks (d each)
+    int32_t *done;       // completion counter of the final reduction (0 between passes)
+    int32_t grid;        // blocks of the row kernel: icd_row_grid(n_tasks, d)
+};
+int32_t icd_row_grid(int32_t n_tasks, int32_t d);
+int32_t icd_split_grid(int32_t n_split);
+cudaError_t launch_icd(const IcdArgs &a, cudaStream_t s);
+// Kernel attributes of the iCD kernels; call once outside any stream capture.
+cudaError_t icd_prepare();
 
 // One fold-in request inside the server's workspace arena (byte offsets; the
 // items start at arena + off, the others are relative to that).

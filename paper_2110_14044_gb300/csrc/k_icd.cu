@@ -1,0 +1,319 @@
+// iCD (Algorithm 2; Eqs. 5-7): the b = 1 end point of the block step, as its
+// own pass per coordinate instead of the general path's per-block Gramian,
+// row-term, statistics and solve kernels.
+//
+// For coordinate f, a pass over the rows of one side (users, then items) needs
+// the column g = G^F[:, f] = sum_j f_j f_{j,f} of the fixed side's Gramian and
+// computes, per row r (Eq. 6),
+//   num = alpha0 <x_r, g> + lambda_r x_{r,f} + sum_{s in S_r} alpha_s e_s f_{c_s,f}
+//   den = alpha0 g_f + lambda_r + sum_{s in S_r} alpha_s f_{c_s,f}^2
+//   delta = num / den,  x_{r,f} -= delta,  e_s -= delta f_{c_s,f}   (Eqs. 5, 7)
+// The Gramian column the next pass needs (the updated side's column f for the
+// item pass; H's column f + 1 for the next user pass) is a sum over the rows
+// this pass updates, so each pass forms it on the way: every warp adds
+// x'_{r,fn} x'_r for its rows, the blocks' partials are summed in a fixed
+// order by the last block to finish.  Rows are assigned to warps statically
+// (task t to warp t mod #warps over the length-sorted task list), so the sums
+// do not depend on timing.  Long rows are cut into chunks (as in the general
+// path): the row kernel stores each chunk's two partial sums; a split kernel
+// sums them in chunk order, solves and applies; a residual kernel updates the
+// residuals of the long rows' pieces.
+#include "ials_internal.cuh"
+
+#include <algorithm>
+
+namespace ials {
+
+namespace {
+
+constexpr int kIcdWarps = 8;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// <x_r, g> with g in shared memory; x_r row-major (d % 4 == 0).  Warp-uniform result.
+__device__ __forceinline__ float row_dot(const float *__restrict__ x, const float *g, int d, int lane) {
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    const float4 *g4 = reinterpret_cast<const float4 *>(g);
+    float acc = 0.f;
+    for (int v = lane; v < (d >> 2); v += 32) {
+        const float4 a = x4[v], b = g4[v];
+        acc = fmaf(a.x, b.x, acc);
+        acc = fmaf(a.y, b.y, acc);
+        acc = fmaf(a.z, b.z, acc);
+        acc = fmaf(a.w, b.w, acc);
+    }
+    return warp_sum(acc);
+}
+
+// part[k] += coef * x'_k for the updated row (x'_f = xf_new), lanes over float4 chunks.
+__device__ __forceinline__ void add_row(float *part, const float *__restrict__ x, int d, int f, float xf_new,
+                                        float coef, int lane) {
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    float4 *p4 = reinterpret_cast<float4 *>(part);
+    for (int v = lane; v < (d >> 2); v += 32) {
+        float4 a = x4[v];
+        if ((f >> 2) == v) {
+            const int q = f & 3;
+            if (q == 0) a.x = xf_new;
+            else if (q == 1) a.y = xf_new;
+            else if (q == 2) a.z = xf_new;
+            else a.w = xf_new;
+        }
+        float4 p = p4[v];
+        p.x = fmaf(coef, a.x, p.x);
+        p.y = fmaf(coef, a.y, p.y);
+        p.z = fmaf(coef, a.z, p.z);
+        p.w = fmaf(coef, a.w, p.w);
+        p4[v] = p;
+    }
+}
+
+// The last block to finish sums the npart partial columns (fixed order) into
+// g_out and resets the counter.  Called by every thread of every block after
+// its partial is written.
+__device__ __forceinline__ void last_block_reduce(const IcdArgs &a, int npart) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(a.done, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int d = a.s.d;
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+        float t = 0.f;
+        for (int p = 0; p < npart; ++p) t += __ldcg(a.gpart + (int64_t)p * d + k);
+        a.g_out[k] = t;
+    }
+    if (threadIdx.x == 0) *a.done = 0;
+}
+
+// Per task: the coordinate-f statistics of a row (or of a chunk of a long row,
+// stored to its slot), then for whole rows the update, the residual update and
+// the Gramian contribution.  Shared: g (d), one partial column per warp (d each).
+template <bool PERM, bool HAS_A>
+__global__ void __launch_bounds__(32 * kIcdWarps) k_icd_rows(const IcdArgs a) {
+    extern __shared__ float4 smem4[];
+    float *g = reinterpret_cast<float *>(smem4);
+    const int d = a.s.d, f = a.f, fn = a.fn;
+    float *wpart = g + d + (threadIdx.x >> 5) * d;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < d; k += blockDim.x) g[k] = a.g_in[k];
+    for (int k = lane; k < d; k += 32) wpart[k] = 0.f;
+    __syncthreads();
+    const StepArgs &s = a.s;
+    const float gf = g[f];
+    const int nwarps = gridDim.x * kIcdWarps;
+    for (int t = blockIdx.x * kIcdWarps + warp; t < s.n_tasks; t += nwarps) {
+        const Task tk = s.tasks[t];
+        float num = 0.f, den = 0.f;
+        constexpr int KEEP = 4;  // interactions kept in registers for the residual update: 32 * KEEP
+        int qk[KEEP];
+        float fk[KEEP];
+        for (int j = 0; j * 32 < tk.len; ++j) {
+            const int i = j * 32 + lane;
+            int q = -1;
+            float fc = 0.f;
+            if (i < tk.len) {
+                const int64_t p = tk.begin + i;
+                q = PERM ? s.pos[p] : (int)p;
+                fc = s.F[(int64_t)s.idx[p] * d + f];
+                const float al = HAS_A ? s.alpha[q] : 1.f;
+                num = fmaf(al * s.e[q], fc, num);
+                den = fmaf(al * fc, fc, den);
+            }
+            if (j < KEEP) {
+#pragma unroll
+                for (int u = 0; u < KEEP; ++u)
+                    if (u == j) { qk[u] = q; fk[u] = fc; }
+            }
+        }
+        num = warp_sum(num);
+        den = warp_sum(den);
+        if (tk.slot >= 0) {  // a chunk of a long row
+            if (lane == 0) {
+                s.part[2 * tk.slot] = num;
+                s.part[2 * tk.slot + 1] = den;
+            }
+            continue;
+        }
+        float *x = s.X + (int64_t)tk.row * d;
+        const float lam = s.lambda * (1.0f + s.nu * (float)tk.len);
+        const float dot = row_dot(x, g, d, lane);
+        const float xf = x[f];
+        num += s.alpha0 * dot + lam * xf;
+        den += s.alpha0 * gf + lam;
+        float delta = 0.f;
+        if (den > 0.f && isfinite(num)) {
+            delta = num / den;
+        } else if (lane == 0) {
+            atomicAdd((unsigned long long *)&s.stats[1], 1ull);
+        }
+        const float xf_new = xf - delta;
+        if (fn >= 0) {
+            const float coef = fn == f ? xf_new : x[fn];
+            add_row(wpart, x, d, f, xf_new, coef, lane);
+        }
+        __syncwarp();
+        if (lane == 0) x[f] = xf_new;
+        for (int j = 0; j * 32 < tk.len; ++j) {
+            const int i = j * 32 + lane;
+            if (j < KEEP) {
+                int q = -1;
+                float fc = 0.f;
+#pragma unroll
+                for (int u = 0; u < KEEP; ++u)
+                    if (u == j) { q = qk[u]; fc = fk[u]; }
+                if (q >= 0) s.e[q] = fmaf(-delta, fc, s.e[q]);
+            } else if (i < tk.len) {
+                const int64_t p = tk.begin + i;
+                const int q = PERM ? s.pos[p] : (int)p;
+                s.e[q] = fmaf(-delta, s.F[(int64_t)s.idx[p] * d + f], s.e[q]);
+            }
+        }
+    }
+    if (fn < 0) return;
+    __syncthreads();
+    // warp partials in warp order -> this block's partial column
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+        float t = 0.f;
+        for (int w = 0; w < kIcdWarps; ++w) t += g[d + w * d + k];
+        a.gpart[(int64_t)blockIdx.x * d + k] = t;
+    }
+    if (s.n_split == 0) last_block_reduce(a, gridDim.x);
+}
+
+// Long rows: one warp per row sums the chunks' partial sums in chunk order,
+// forms the dense terms and the update, applies it and records delta; each
+// block sums its rows' Gramian contributions in row order into one partial
+// column (after the row kernel's), and the last block reduces all partials.
+__global__ void __launch_bounds__(32 * kIcdWarps) k_icd_split(const IcdArgs a) {
+    extern __shared__ float4 smem4[];
+    float *g = reinterpret_cast<float *>(smem4);
+    const int d = a.s.d, f = a.f, fn = a.fn;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *wpart = g + d + warp * d;
+    for (int k = threadIdx.x; k < d; k += blockDim.x) g[k] = a.g_in[k];
+    for (int k = lane; k < d; k += 32) wpart[k] = 0.f;
+    __syncthreads();
+    const StepArgs &s = a.s;
+    const int nwarps = gridDim.x * kIcdWarps;
+    for (int i = blockIdx.x * kIcdWarps + warp; i < s.n_split; i += nwarps) {
+        const SplitRow sr = s.split[i];
+        float num = 0.f, den = 0.f;
+        for (int k = 0; k < sr.nslots; ++k) {
+            num += s.part[2 * (sr.slot0 + k)];
+            den += s.part[2 * (sr.slot0 + k) + 1];
+        }
+        float *x = s.X + (int64_t)sr.row * d;
+        const float lam = s.lambda * (1.0f + s.nu * (float)sr.len);
+        const float dot = row_dot(x, g, d, lane);
+        const float xf = x[f];
+        num += s.alpha0 * dot + lam * xf;
+        den += s.alpha0 * g[f] + lam;
+        float delta = 0.f;
+        if (den > 0.f && isfinite(num)) {
+            delta = num / den;
+        } else if (lane == 0) {
+            atomicAdd((unsigned long long *)&s.stats[1], 1ull);
+        }
+        const float xf_new = xf - delta;
+        if (fn >= 0) add_row(wpart, x, d, f, xf_new, fn == f ? xf_new : x[fn], lane);
+        __syncwarp();
+        if (lane == 0) {
+            x[f] = xf_new;
+            s.delta[i] = delta;
+        }
+    }
+    if (fn < 0) return;
+    __syncthreads();
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+        float t = 0.f;
+        for (int w = 0; w < kIcdWarps; ++w) t += g[d + w * d + k];
+        a.gpart[(int64_t)(a.grid + blockIdx.x) * d + k] = t;
+    }
+    last_block_reduce(a, a.grid + gridDim.x);
+}
+
+// Residual update of the long rows, one warp per piece of at most 128 interactions.
+template <bool PERM>
+__global__ void __launch_bounds__(256) k_icd_split_resid(const IcdArgs a) {
+    const StepArgs &s = a.s;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < s.n_stasks; t += nwarps) {
+        const Task tk = s.stasks[t];
+        const float delta = s.delta[tk.srow];
+        for (int i = lane; i < tk.len; i += 32) {
+            const int64_t p = tk.begin + i;
+            const int q = PERM ? s.pos[p] : (int)p;
+            s.e[q] = fmaf(-delta, s.F[(int64_t)s.idx[p] * s.d + a.f], s.e[q]);
+        }
+    }
+}
+
+constexpr int kIcdMaxSmem = (int)(sizeof(float) * 4096 * (1 + kIcdWarps));  // d <= 4096
+
+template <bool PERM, bool HAS_A>
+cudaError_t launch_icd_t(const IcdArgs &a0, cudaStream_t st) {
+    IcdArgs a = a0;
+    const size_t smem = sizeof(float) * (size_t)a.s.d * (1 + kIcdWarps);
+    prof_mark(a.s.prof, K_SPARSE, st);
+    k_icd_rows<PERM, HAS_A><<<a.grid, 32 * kIcdWarps, smem, st>>>(a);
+    prof_mark(a.s.prof, -1, st);
+    if (a.s.n_split > 0) {
+        prof_mark(a.s.prof, K_SPLIT_SOLVE, st);
+        k_icd_split<<<icd_split_grid(a.s.n_split), 32 * kIcdWarps, smem, st>>>(a);
+        prof_mark(a.s.prof, K_SPLIT_RESID, st);
+        const int g3 = (int)std::min<int64_t>((a.s.n_stasks + 7) / 8, 152 * 8);
+        k_icd_split_resid<PERM><<<g3 > 0 ? g3 : 1, 256, 0, st>>>(a);
+        prof_mark(a.s.prof, -1, st);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int32_t icd_row_grid(int32_t n_tasks, int32_t d) {
+    // one block per SM (two when d is small enough for the shared partials), never
+    // more blocks than eight-task groups
+    const int per_sm = d <= 2048 ? 2 : 1;
+    int32_t g = 152 * per_sm;
+    const int32_t need = (n_tasks + kIcdWarps - 1) / kIcdWarps;
+    if (g > need) g = need;
+    return g > 0 ? g : 1;
+}
+
+int32_t icd_split_grid(int32_t n_split) {
+    int32_t g = (n_split + kIcdWarps - 1) / kIcdWarps;
+    if (g > 38) g = 38;
+    return g > 0 ? g : 1;
+}
+
+cudaError_t icd_prepare() {
+    static cudaError_t done = cudaErrorNotReady;
+    if (done == cudaSuccess) return done;
+    cudaError_t e = cudaSuccess;
+    const auto set = [&](const void *k) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kIcdMaxSmem);
+    };
+    set((const void *)k_icd_rows<false, false>);
+    set((const void *)k_icd_rows<false, true>);
+    set((const void *)k_icd_rows<true, false>);
+    set((const void *)k_icd_rows<true, true>);
+    set((const void *)k_icd_split);
+    done = e;
+    return e;
+}
+
+cudaError_t launch_icd(const IcdArgs &a, cudaStream_t s) {
+    const bool perm = a.s.pos != nullptr, wa = a.s.alpha != nullptr;
+    if (perm) return wa ? launch_icd_t<true, true>(a, s) : launch_icd_t<true, false>(a, s);
+    return wa ? launch_icd_t<false, true>(a, s) : launch_icd_t<false, false>(a, s);
+}
+
+}  // namespace ials

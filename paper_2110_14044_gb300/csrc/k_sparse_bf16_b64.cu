@@ -3,6 +3,6 @@
 
 namespace ials {
 cudaError_t launch_sparse_bf16_b64(const StepArgs &a, cudaStream_t s) {
-    return a.pos ? launch_sparse_cta_bf16_all<64, true>(a, s) : launch_sparse_cta_bf16_all<64, false>(a, s);
+    return launch_sparse_cta_bf16_dispatch<64>(a, s);
 }
 }  // namespace ials

@@ -1,20 +1,10 @@
-// Sparse block step of Algorithm 3 for block sizes B = 64 and 128 (one CTA per task).
-//
-// The step is the one of k_sparse_impl.cuh (Eqs. 11-12, Newton solve, apply,
-// residual update); only the work layout changes because the b x b statistics
-// no longer fit a warp's registers:
-//  * accumulation: A_r is cut into 8 x 8 tiles; the NTL = (B/8)(B/8+1)/2 tiles
-//    on or below the diagonal are owned by NTL threads of each of NG
-//    interaction groups (group g takes staged interactions g, g + NG, ...).
-//    Slices are gathered with cp.async into two staging buffers.  Group
-//    partials are summed in group order into a shared (B+1) x (B+4) matrix M
-//    whose last row holds the gradient.
-//  * solve: a blocked right-looking Cholesky of M in shared memory with panel
-//    width 8 (diagonal block by one warp, panel by one thread per row, trailing
-//    update by 2 x 8 output units).  Row B rides along, so the forward
-//    substitution L z = g falls out of the factorisation; the backward
-//    substitution runs panel by panel from the bottom.
-//  * the same routine, templated on double, is the FP64 retry.
+// Shared pieces of the CTA-per-row block step for block sizes B = 64 and 128:
+// the staged gathers and residual updates, the shared-memory blocked Cholesky
+// in 16-column panels (used by the fold-in kernel), and the FP64 re-solve of
+// rows whose FP32 pivot failed: statistics accumulated from scratch in FP64 by
+// 8 x 8 tile owners, a blocked Cholesky in panels of 8 in FP64 (the routine
+// cta_cholesky, templated on the type), apply and residual update.  The FP32
+// and BF16 kernels themselves are in k_sparse_rc.cuh and k_sparse_cta_bf16.cuh.
 #pragma once
 
 #include "k_sparse_impl.cuh"
@@ -337,7 +327,7 @@ __device__ void cta_backsolve16(const float *M, const float *invd, float *x) {
 
 // Adds alpha0 G_pipi + lambda I to rows 0..B-1 of M (lower part) and R_r to row B;
 // records the diagonal in diag0.
-template <int B, int SM, typename T>
+template <int B, int SM, typename T, bool WITH_R = true>
 __device__ void cta_dense_terms(const StepArgs &a, T *M, T *diag0, int row, T lam) {
     for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
         const int i = e / B, j = e % B;
@@ -349,7 +339,8 @@ __device__ void cta_dense_terms(const StepArgs &a, T *M, T *diag0, int row, T la
         }
         M[i * SM + j] = v;
     }
-    for (int j = threadIdx.x; j < B; j += blockDim.x) M[B * SM + j] += (T)a.R[(int64_t)row * B + j];
+    if (WITH_R)
+        for (int j = threadIdx.x; j < B; j += blockDim.x) M[B * SM + j] += (T)a.R[(int64_t)row * B + j];
 }
 
 // Gather `cnt` slices starting at CSR position s0 into buf (all threads).
@@ -435,211 +426,10 @@ __device__ void cta_residual_update2(const StepArgs &a, int64_t s0, int len, int
     }
 }
 
-// Two resident CTAs per SM (at B = 128 registers are capped at 96).
-template <int B, bool PERM, bool HAS_A>
-__global__ void __launch_bounds__(CtaCfg<B>::THREADS, 2) k_sparse_cta(const StepArgs a) {
-    using C = CtaCfg<B>;
-    constexpr int SB = C::SB, CH = C::CH;
-    extern __shared__ float4 smem4[];
-    float *smem = reinterpret_cast<float *>(smem4);
-    float *buf0 = smem;                      // staging buffer bi at buf0 + bi * BUF
-    float *she = smem + 2 * C::BUF;          // residuals (weighted) [2][CH]
-    float *sha = she + 2 * CH;               // weights [2][CH]
-    float *M = sha + 2 * CH;                 // (B+1) x SB
-    float *diag0 = M + (B + 1) * SB;
-    float *invd = diag0 + B;
-    float *xv = invd + B;
-    int *flag = reinterpret_cast<int *>(xv + B);  // [0] task, [1] bad
-    const int tid = threadIdx.x;
-    const bool active = tid < C::ACTIVE;
-    const int grp = active ? tid / C::NTL : C::NG;
-    const int kstart = active ? grp : C::CH;  // idle threads skip the accumulation
-    int ti = 0, tj = 0;
-    tri_index(tid % C::NTL, ti, tj);
-    // the next task index is fetched while the current task runs
-    if (tid == 0) flag[0] = atomicAdd(a.counter, 1);
-    for (;;) {
-        __syncthreads();
-        const int tsk = flag[0];
-        if (tsk >= a.n_tasks) break;
-        __syncthreads();  // every thread has read flag[0]
-        if (tid == 0) flag[0] = atomicAdd(a.counter, 1);
-        const Task tk = a.tasks[tsk];
-        const int nch = (tk.len + CH - 1) / CH;
-        float acc[8][8], gacc[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            gacc[i] = 0.f;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-        }
-        const float lam = a.lambda * (1.0f + a.nu * (float)tk.len);
-        if (tk.slot < 0 && grp == 0) {  // whole row: group 0 starts from alpha0 G_pipi + lambda_r I and R_r
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float *gr = a.G + (int64_t)(a.p0 + 8 * ti + i) * B + 8 * tj;
-                const float4 g0 = *reinterpret_cast<const float4 *>(gr);
-                const float4 g1 = *reinterpret_cast<const float4 *>(gr + 4);
-                acc[i][0] = a.alpha0 * g0.x; acc[i][1] = a.alpha0 * g0.y;
-                acc[i][2] = a.alpha0 * g0.z; acc[i][3] = a.alpha0 * g0.w;
-                acc[i][4] = a.alpha0 * g1.x; acc[i][5] = a.alpha0 * g1.y;
-                acc[i][6] = a.alpha0 * g1.z; acc[i][7] = a.alpha0 * g1.w;
-                if (ti == tj) acc[i][i] += lam;
-                if (tj == 0) gacc[i] = a.R[(int64_t)tk.row * B + 8 * ti + i];
-            }
-        }
-        auto meta = [&](int j, int bi) {  // residual and weight of chunk j into buffer bi (warp 0)
-            const int cnt = min(CH, tk.len - j * CH);
-            if (tid < cnt) {
-                const int64_t s = tk.begin + (int64_t)j * CH + tid;
-                const int64_t q = PERM ? (int64_t)a.pos[s] : s;
-                const float r = a.e[q];
-                const float al = HAS_A ? a.alpha[q] : 1.f;
-                she[bi * CH + tid] = HAS_A ? al * r : r;
-                if (HAS_A) sha[bi * CH + tid] = al;
-            }
-        };
-        if (nch > 0) {
-            meta(0, 0);
-            cta_gather<B>(a, tk.begin, min(CH, tk.len), buf0);
-            cp_async_commit();
-        }
-        for (int ch = 0; ch < nch; ++ch) {
-            const int bi = ch & 1;
-            cp_async_wait_all();
-            __syncthreads();
-            if (ch + 1 < nch) {
-                meta(ch + 1, bi ^ 1);
-                cta_gather<B>(a, tk.begin + (int64_t)(ch + 1) * CH, min(CH, tk.len - (ch + 1) * CH),
-                              buf0 + (bi ^ 1) * C::BUF);
-                cp_async_commit();
-            }
-            const int cnt = min(CH, tk.len - ch * CH);
-            const float *bp = buf0 + bi * C::BUF;
-            for (int k = kstart; k < cnt; k += C::NG) {
-                const float *xk = bp + k * SB;
-                float xa[8], xb[8];
-                load_seg<8>(xk + 8 * ti, xa);
-                load_seg<8>(xk + 8 * tj, xb);
-                const float ek = she[bi * CH + k];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) gacc[i] += ek * xa[i];
-                if (HAS_A) {
-                    const float ak = sha[bi * CH + k];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) xa[i] *= ak;
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] += xa[i] * xb[j];
-            }
-        }
-        __syncthreads();
-        // fixed-order sum of the group partials into M; gradient into row B
-#pragma unroll 1
-        for (int ph = 0; ph < C::NG; ++ph) {
-            if (grp == ph) {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) store_tile<8>(M + (8 * ti + i) * SB + 8 * tj, acc[i], ph > 0);
-                if (tj == 0) {
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        M[B * SB + 8 * ti + i] = (ph > 0 ? M[B * SB + 8 * ti + i] : 0.f) + gacc[i];
-                }
-            }
-            __syncthreads();
-        }
-        if (tk.slot >= 0) {  // a chunk of a long row: store the partial statistics
-            float *P = a.part + (int64_t)tk.slot * (B * B + B);
-            for (int e = tid; e < B * B; e += blockDim.x) {
-                const int i = e / B, j = e % B;
-                P[e] = j <= i ? M[i * SB + j] : 0.f;
-            }
-            for (int j = tid; j < B; j += blockDim.x) P[B * B + j] = M[B * SB + j];
-            continue;
-        }
-        if (tid == 0) flag[1] = a.force_fp64 ? 1 : 0;
-        for (int i = tid; i < B; i += blockDim.x) diag0[i] = M[i * SB + i];  // the dense terms are in already
-        __syncthreads();
-        cta_chol16<B, SB>(M, invd, diag0, &flag[1], 1e-5f);
-        if (flag[1]) {  // CTA-uniform: queue the row for the FP64 re-solve
-            if (tid == 0) {
-                const int i = atomicAdd(a.retry, 1);
-                a.retry[1 + i] = tk.row;
-            }
-            continue;
-        }
-        for (int j = tid; j < B; j += blockDim.x) xv[j] = M[B * SB + j];
-        __syncthreads();
-        cta_backsolve16<B, SB>(M, invd, xv);
-        if (!__syncthreads_and(tid >= B || isfinite(xv[tid]))) {
-            if (tid == 0) {
-                const int i = atomicAdd(a.retry, 1);
-                a.retry[1 + i] = tk.row;
-            }
-            continue;
-        }
-        for (int j = tid; j < B; j += blockDim.x) apply_delta(a.X, a.Xh, a.Xl, (int64_t)tk.row * a.d + a.p0 + j, xv[j]);
-        cta_residual_update2<B, PERM>(a, tk.begin, tk.len, nch, xv, buf0);
-    }
-}
-
-// One block per split row: partial slots summed in slot order, then the CTA solve.
-template <int B>
-__global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_split_solve_cta(const StepArgs a) {
-    using C = CtaCfg<B>;
-    constexpr int SB = C::SB;
-    extern __shared__ float4 smem4[];
-    float *smem = reinterpret_cast<float *>(smem4);
-    float *M = smem + 2 * C::BUF + 4 * C::CH;
-    float *diag0 = M + (B + 1) * SB;
-    float *invd = diag0 + B;
-    float *xv = invd + B;
-    int *flag = reinterpret_cast<int *>(xv + B);
-    const int tid = threadIdx.x;
-    for (int i = blockIdx.x; i < a.n_split; i += gridDim.x) {
-        const SplitRow sr = a.split[i];
-        const float *P0 = a.part + (int64_t)sr.slot0 * (B * B + B);
-        for (int e = tid; e < B * B + B; e += blockDim.x) {
-            float t = 0.f;
-            for (int sl = 0; sl < sr.nslots; ++sl) t += P0[(int64_t)sl * (B * B + B) + e];
-            if (e < B * B) M[(e / B) * SB + (e % B)] = t;
-            else M[B * SB + (e - B * B)] = t;
-        }
-        if (tid == 0) flag[1] = a.force_fp64 ? 1 : 0;
-        __syncthreads();
-        const float lam = a.lambda * (1.0f + a.nu * (float)sr.len);
-        cta_dense_terms<B, SB, float>(a, M, diag0, sr.row, lam);
-        __syncthreads();
-        cta_chol16<B, SB>(M, invd, diag0, &flag[1], 1e-5f);
-        bool ok = !flag[1];
-        if (ok) {
-            for (int j = tid; j < B; j += blockDim.x) xv[j] = M[B * SB + j];
-            __syncthreads();
-            cta_backsolve16<B, SB>(M, invd, xv);
-            for (int j = 0; j < B; ++j) ok = ok && isfinite(xv[j]);
-        }
-        if (!ok) {
-            if (tid == 0) {
-                const int q = atomicAdd(a.retry, 1);
-                a.retry[1 + q] = sr.row;
-            }
-            for (int j = tid; j < B; j += blockDim.x) a.delta[(int64_t)i * B + j] = 0.f;
-        } else {
-            for (int j = tid; j < B; j += blockDim.x) {
-                apply_delta(a.X, a.Xh, a.Xl, (int64_t)sr.row * a.d + a.p0 + j, xv[j]);
-                a.delta[(int64_t)i * B + j] = xv[j];
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // FP64 re-solve of queued rows: statistics accumulated from scratch in FP64 by
 // the tile owners (one group, reading slices straight from global memory), the
 // blocked Cholesky in FP64, apply and residual update.
-template <int B, bool PERM, bool HAS_A>
+template <int B, bool PERM, bool HAS_A, bool DIRECT = false>
 __global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_retry_cta(const StepArgs a) {
     using C = CtaCfg<B>;
     constexpr int SM = B + 1;
@@ -670,7 +460,7 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_retry_cta(const StepArgs
                 const int64_t r = PERM ? (int64_t)a.pos[s] : s;
                 const float *f = a.F + (int64_t)a.idx[s] * a.d + a.p0;
                 const double al = HAS_A ? (double)a.alpha[r] : 1.0;
-                const double er = al * (double)a.e[r];
+                const double er = al * (double)(DIRECT ? (a.y ? a.y[r] : 1.f) : a.e[r]);
                 double xa[8], xb[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) { xa[i] = f[8 * ti + i]; xb[i] = f[8 * tj + i]; }
@@ -691,7 +481,7 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_retry_cta(const StepArgs
         if (tid == 0) flag[1] = 0;
         __syncthreads();
         const double lam = (double)a.lambda * (1.0 + (double)a.nu * (double)(end - beg));
-        cta_dense_terms<B, SM, double>(a, M, diag0, row, lam);
+        cta_dense_terms<B, SM, double, !DIRECT>(a, M, diag0, row, lam);
         __syncthreads();
         cta_cholesky<B, SM, double>(M, invd, diag0, &flag[1], 1e-13);
         bool ok = !flag[1];
@@ -708,10 +498,11 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_retry_cta(const StepArgs
         }
         for (int j = tid; j < B; j += blockDim.x) {
             xf[j] = (float)xd[j];
-            apply_delta(a.X, a.Xh, a.Xl, (int64_t)row * a.d + a.p0 + j, xf[j]);
+            if (DIRECT) set_value(a.X, a.Xh, a.Xl, (int64_t)row * a.d + a.p0 + j, xf[j]);
+            else apply_delta(a.X, a.Xh, a.Xl, (int64_t)row * a.d + a.p0 + j, xf[j]);
         }
         __syncthreads();
-        cta_residual_update<B, PERM>(a, beg, (int)(end - beg), xf, buf);
+        if (!DIRECT) cta_residual_update<B, PERM>(a, beg, (int)(end - beg), xf, buf);
         if (tid == 0) atomicAdd((unsigned long long *)&a.stats[0], 1ull);
     }
 }
@@ -719,54 +510,6 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_retry_cta(const StepArgs
 template <int B>
 constexpr int retry_cta_smem() {
     return CtaCfg<B>::BUF * 4 + ((B + 1) * (B + 1) + 3 * B) * 8 + 16 + B * 4;
-}
-
-template <int B, bool PERM, bool HAS_A>
-cudaError_t launch_sparse_cta_all(const StepArgs &a, cudaStream_t s) {
-    using C = CtaCfg<B>;
-    static bool attr_done = false;
-    static int per_sm = 0;
-    if (!attr_done) {
-        cudaError_t e;
-        if ((e = cudaFuncSetAttribute(k_sparse_cta<B, PERM, HAS_A>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_split_solve_cta<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      C::SMEM_BYTES)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_retry_cta<B, PERM, HAS_A>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, retry_cta_smem<B>())) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sparse_cta<B, PERM, HAS_A>,
-                                                               C::THREADS, C::SMEM_BYTES)) != cudaSuccess) return e;
-        if (per_sm < 1) per_sm = 1;
-        attr_done = true;
-    }
-    if (a.n_tasks > 0) {
-        int grid = 152 * per_sm;
-        if (grid > a.n_tasks) grid = a.n_tasks;
-        prof_mark(a.prof, K_SPARSE, s);
-        k_sparse_cta<B, PERM, HAS_A><<<grid, C::THREADS, C::SMEM_BYTES, s>>>(a);
-        prof_mark(a.prof, -1, s);
-    }
-    if (a.n_split > 0) {
-        const int g2 = a.n_split < 152 * 4 ? a.n_split : 152 * 4;
-        prof_mark(a.prof, K_SPLIT_SOLVE, s);
-        k_split_solve_cta<B><<<g2, C::THREADS, C::SMEM_BYTES, s>>>(a);
-        prof_mark(a.prof, -1, s);
-    }
-    {  // always called: the first call sizes the grid, outside any stream capture
-        const cudaError_t e = launch_split_resid_reg<B, PERM>(a, s);
-        if (e != cudaSuccess) return e;
-    }
-    prof_mark(a.prof, K_RETRY, s);
-    k_retry_cta<B, PERM, HAS_A><<<76, C::THREADS, retry_cta_smem<B>(), s>>>(a);
-    prof_mark(a.prof, -1, s);
-    return cudaGetLastError();
-}
-
-template <int B>
-cudaError_t launch_sparse_cta_dispatch(const StepArgs &a, cudaStream_t s) {
-    const bool perm = a.pos != nullptr, wa = a.alpha != nullptr;
-    if (perm) return wa ? launch_sparse_cta_all<B, true, true>(a, s) : launch_sparse_cta_all<B, true, false>(a, s);
-    return wa ? launch_sparse_cta_all<B, false, true>(a, s) : launch_sparse_cta_all<B, false, false>(a, s);
 }
 
 }  // namespace ials

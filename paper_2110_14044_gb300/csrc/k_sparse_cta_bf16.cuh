@@ -12,14 +12,14 @@
 // which keeps its fragments and accumulators in registers; a warp loads only
 // the 16-column blocks its tiles touch.  For a whole row the accumulators start
 // from the dense terms alpha0 G_pipi + lambda_r I and R_r.  The fragments go to
-// a shared FP32 matrix, and the solve, the apply and the residual update are those of
-// k_sparse_cta.cuh: blocked Cholesky in 16-column panels with the right-hand
-// side as an extra row, backward substitution, and the residual update from
-// the staged (hi + lo) slices.
+// a shared FP32 matrix, from which the owners of the 8 x 8 tiles of
+// k_sparse_rc.cuh take them into registers for its blocked Cholesky and
+// substitutions; the residual update uses the staged (hi + lo) slices.
 #pragma once
 
 #include "k_sparse_bf16.cuh"
 #include "k_sparse_cta.cuh"
+#include "k_sparse_rc.cuh"
 
 namespace ials {
 
@@ -35,8 +35,9 @@ struct CtaBfCfg {
     static constexpr int BUF = 2 * TILE;    // one staging buffer: hi tile, then lo tile
     static constexpr int SM = B + 4;        // float row stride of the shared matrix (= 4 mod 32)
     static constexpr int M_FLOATS = (B + 1) * SM;
-    static constexpr int SMEM_BYTES = 2 * BUF * 2 + (M_FLOATS + 3 * B) * 4 + 16;
-    static_assert(SM % 32 == 4, "panel layout of cta_chol16");
+    static constexpr int SMEM_BYTES = 2 * BUF * 2 + (M_FLOATS + B) * 4 + 16;
+    static_assert(M_FLOATS >= 2 * RegChol<B>::PANEL, "the panels reuse M");
+    static_assert(THREADS >= RegChol<B>::NTL, "one tile per thread");
 };
 
 // Compile-time tile list of warp W: the tiles of rows I1 = W / 2 and I2 = MT - 1 - W / 2
@@ -216,18 +217,19 @@ __device__ __forceinline__ void cta_bf_gather(const StepArgs &a, int64_t s0, int
     }
 }
 
-template <int B, bool PERM>
+template <int B, bool PERM, bool DIRECT>
 __global__ void __launch_bounds__(CtaBfCfg<B>::THREADS, 2) k_sparse_cta_bf16(const StepArgs a) {
     using C = CtaBfCfg<B>;
     constexpr int SBH = C::SBH, CH = C::CH, SM = C::SM, NPT = C::NPT;
     extern __shared__ float4 smem4[];
     __nv_bfloat16 *bufs = reinterpret_cast<__nv_bfloat16 *>(smem4);  // buffer bi: hi at bufs + bi * BUF, lo + TILE
     float *M = reinterpret_cast<float *>(bufs + 2 * C::BUF);
-    float *diag0 = M + C::M_FLOATS;
-    float *invd = diag0 + B;
-    float *xv = invd + B;
+    float *xv = M + C::M_FLOATS;
     int *flag = reinterpret_cast<int *>(xv + B);  // [0] next task, [1] bad pivot
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x, nw = nt >> 5;
+    const bool own = tid < RegChol<B>::NTL;
+    int ti = 0, tj = 0;
+    tri_index(tid % RegChol<B>::NTL, ti, tj);
     for (int i = tid; i < 2 * C::BUF * 2 / 16; i += nt)
         reinterpret_cast<uint4 *>(bufs)[i] = make_uint4(0u, 0u, 0u, 0u);  // padding columns stay zero
     if (tid == 0) flag[0] = atomicAdd(a.counter, 1);  // the next task is fetched while one runs
@@ -247,7 +249,13 @@ __global__ void __launch_bounds__(CtaBfCfg<B>::THREADS, 2) k_sparse_cta_bf16(con
 #pragma unroll
         for (int q = 0; q < 4; ++q) gac[q] = 0.f;
         const float lam = a.lambda * (1.0f + a.nu * (float)tk.len);
-        if (tk.slot < 0) cta_bf_init_any<B>(warp, acc, gac, a, tk.row, lam, lane);
+        if (tk.slot < 0) {
+            cta_bf_init_any<B>(warp, acc, gac, a, tk.row, lam, lane);
+            if (DIRECT) {  // Eq. 3: the right-hand side is sum alpha y f, no row term
+#pragma unroll
+                for (int q = 0; q < 4; ++q) gac[q] = 0.f;
+            }
+        }
         // chunk j into buffer bi: residual column (hi, lo), zero rows up to the next
         // multiple of 16, and the slices
         auto issue = [&](int j, int bi) {
@@ -258,7 +266,7 @@ __global__ void __launch_bounds__(CtaBfCfg<B>::THREADS, 2) k_sparse_cta_bf16(con
                 if (r < cnt) {
                     const int64_t s = tk.begin + (int64_t)j * CH + r;
                     const int64_t q = PERM ? (int64_t)a.pos[s] : s;
-                    const float e = a.e[q];
+                    const float e = DIRECT ? (a.y ? a.y[q] : 1.f) : a.e[q];
                     const __nv_bfloat16 h = __float2bfloat16_rn(e);
                     th[r * SBH + B] = h;
                     tl[r * SBH + B] = __float2bfloat16_rn(e - __bfloat162float(h));
@@ -295,10 +303,17 @@ __global__ void __launch_bounds__(CtaBfCfg<B>::THREADS, 2) k_sparse_cta_bf16(con
             for (int j = tid; j < B; j += nt) P[B * B + j] = M[B * SM + j];
             continue;
         }
+        // the solve of k_sparse_rc.cuh: owners take their 8 x 8 tile of the system (dense
+        // terms are in already) into registers; M is then free and holds the panels
+        float t[8][8], inv[8];
+        if (own) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) load_seg<8>(M + (8 * ti + i) * SM + 8 * tj, t[i]);
+        }
+        for (int j = tid; j < B; j += nt) xv[j] = M[B * SM + j];
         if (tid == 0) flag[1] = a.force_fp64 ? 1 : 0;
-        for (int i = tid; i < B; i += nt) diag0[i] = M[i * SM + i];  // the dense terms are in already
         __syncthreads();
-        cta_chol16<B, SM>(M, invd, diag0, &flag[1], 1e-5f);
+        rc_factor<B>(t, inv, ti, tj, own, M, xv, &flag[1], 1e-5f);
         if (flag[1]) {  // CTA-uniform: queue the row for the FP64 re-solve
             if (tid == 0) {
                 const int i = atomicAdd(a.retry, 1);
@@ -306,14 +321,18 @@ __global__ void __launch_bounds__(CtaBfCfg<B>::THREADS, 2) k_sparse_cta_bf16(con
             }
             continue;
         }
-        for (int j = tid; j < B; j += nt) xv[j] = M[B * SM + j];
-        __syncthreads();
-        cta_backsolve16<B, SM>(M, invd, xv);
-        if (!__syncthreads_and(tid >= B || isfinite(xv[tid]))) {
+        rc_backsolve<B>(t, inv, ti, tj, own, xv);
+        bool fin = true;
+        for (int j = tid; j < B; j += nt) fin = fin && isfinite(xv[j]);
+        if (!__syncthreads_and(fin)) {
             if (tid == 0) {
                 const int i = atomicAdd(a.retry, 1);
                 a.retry[1 + i] = tk.row;
             }
+            continue;
+        }
+        if (DIRECT) {  // the solution is the row itself
+            for (int j = tid; j < B; j += nt) set_value(a.X, a.Xh, a.Xl, (int64_t)tk.row * a.d + a.p0 + j, xv[j]);
             continue;
         }
         for (int j = tid; j < B; j += nt) apply_delta(a.X, a.Xh, a.Xl, (int64_t)tk.row * a.d + a.p0 + j, xv[j]);
@@ -360,8 +379,9 @@ __global__ void __launch_bounds__(CtaBfCfg<B>::THREADS, 2) k_sparse_cta_bf16(con
 }
 
 // Whole sparse part of a BF16 block-side step at B = 64, 128: the CTA kernel,
-// then long rows (slot sums and CTA solve), their residual update, FP64 retry.
-template <int B, bool PERM>
+// then long rows (slot sums and the register-tile solve), their residual
+// update (not for DIRECT), FP64 retry.
+template <int B, bool PERM, bool DIRECT>
 cudaError_t launch_sparse_cta_bf16_all(const StepArgs &a, cudaStream_t s) {
     using C = CtaBfCfg<B>;
     using CF = CtaCfg<B>;
@@ -369,13 +389,13 @@ cudaError_t launch_sparse_cta_bf16_all(const StepArgs &a, cudaStream_t s) {
     static int per_sm = 0;
     if (!attr_done) {
         cudaError_t e;
-        if ((e = cudaFuncSetAttribute(k_sparse_cta_bf16<B, PERM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if ((e = cudaFuncSetAttribute(k_sparse_cta_bf16<B, PERM, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       C::SMEM_BYTES)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_split_solve_cta<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      CF::SMEM_BYTES)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_retry_cta<B, PERM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if ((e = cudaFuncSetAttribute(k_split_solve_rc<B, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      RcCfg<B>::SMEM_BYTES)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_retry_cta<B, PERM, false, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       retry_cta_smem<B>())) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sparse_cta_bf16<B, PERM>, C::THREADS,
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sparse_cta_bf16<B, PERM, DIRECT>, C::THREADS,
                                                                C::SMEM_BYTES)) != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         attr_done = true;
@@ -384,23 +404,29 @@ cudaError_t launch_sparse_cta_bf16_all(const StepArgs &a, cudaStream_t s) {
         int grid = 152 * per_sm;
         if (grid > a.n_tasks) grid = a.n_tasks;
         prof_mark(a.prof, K_SPARSE, s);
-        k_sparse_cta_bf16<B, PERM><<<grid, C::THREADS, C::SMEM_BYTES, s>>>(a);
+        k_sparse_cta_bf16<B, PERM, DIRECT><<<grid, C::THREADS, C::SMEM_BYTES, s>>>(a);
         prof_mark(a.prof, -1, s);
     }
     if (a.n_split > 0) {
         const int g2 = a.n_split < 152 * 4 ? a.n_split : 152 * 4;
         prof_mark(a.prof, K_SPLIT_SOLVE, s);
-        k_split_solve_cta<B><<<g2, CF::THREADS, CF::SMEM_BYTES, s>>>(a);
+        k_split_solve_rc<B, DIRECT><<<g2, RcCfg<B>::THREADS, RcCfg<B>::SMEM_BYTES, s>>>(a);
         prof_mark(a.prof, -1, s);
     }
-    {  // always called: the first call sizes the grid, outside any stream capture
+    if (!DIRECT) {  // always called: the first call sizes the grid, outside any stream capture
         const cudaError_t e = launch_split_resid_reg_bf16<B, PERM>(a, s);
         if (e != cudaSuccess) return e;
     }
     prof_mark(a.prof, K_RETRY, s);
-    k_retry_cta<B, PERM, false><<<76, CF::THREADS, retry_cta_smem<B>(), s>>>(a);
+    k_retry_cta<B, PERM, false, DIRECT><<<76, CF::THREADS, retry_cta_smem<B>(), s>>>(a);
     prof_mark(a.prof, -1, s);
     return cudaGetLastError();
+}
+
+template <int B>
+cudaError_t launch_sparse_cta_bf16_dispatch(const StepArgs &a, cudaStream_t s) {
+    if (a.direct) return a.pos ? launch_sparse_cta_bf16_all<B, true, true>(a, s) : launch_sparse_cta_bf16_all<B, false, true>(a, s);
+    return a.pos ? launch_sparse_cta_bf16_all<B, true, false>(a, s) : launch_sparse_cta_bf16_all<B, false, false>(a, s);
 }
 
 }  // namespace ials
