@@ -144,6 +144,7 @@ struct ials_ctx {
     double *g64a = nullptr, *g64b = nullptr, *g64ws = nullptr;
     // iCD path (b = 1): Gramian columns (two of d), their partials, completion counter
     float *icd_g = nullptr, *icd_gpart = nullptr;
+    float *WT = nullptr, *HT = nullptr;  // transposed factors (d x n), kept current by the passes
     int32_t *icd_done = nullptr;
     cudaGraphExec_t graph = nullptr;
     bool own_stream = false;
@@ -297,6 +298,15 @@ StepArgs step_args(ials_ctx *c, int side, int p0, Profiler *prof) {
 // The iCD path (Algorithm 2) runs for b = 1 unless the general path is forced.
 bool use_icd(const ials_ctx *c) { return c->p.b == 1 && !(c->p.flags & IALS_FLAG_GENERAL); }
 
+// Transposed copies of W and H for the iCD passes (each pass then keeps them current).
+cudaError_t icd_transpose(ials_ctx *c, Profiler *prof) {
+    prof_mark(prof, K_RESIDUAL, c->stream);  // data movement at the epoch start
+    cudaError_t e = launch_transpose(c->W, c->n_users, c->p.d, c->WT, c->stream);
+    if (e == cudaSuccess) e = launch_transpose(c->H, c->n_items, c->p.d, c->HT, c->stream);
+    prof_mark(prof, -1, c->stream);
+    return e;
+}
+
 // One iCD pass: side `side`, coordinate f, fixed-side Gramian column in g_in;
 // forms the updated side's column fn (>= 0) into g_out on the way.
 ials_status icd_pass_enqueue(ials_ctx *c, int side, int f, int fn, const float *g_in, float *g_out,
@@ -310,6 +320,9 @@ ials_status icd_pass_enqueue(ials_ctx *c, int side, int f, int fn, const float *
     a.gpart = c->icd_gpart;
     a.done = c->icd_done;
     a.grid = icd_row_grid(a.s.n_tasks, c->p.d);
+    a.FT = side == 0 ? c->HT : c->WT;
+    a.XT = side == 0 ? c->WT : c->HT;
+    a.n_fixed = side == 0 ? c->n_items : c->n_users;
     IALS_CUDA(launch_icd(a, c->stream), "iCD pass");
     return IALS_OK;
 }
@@ -354,6 +367,7 @@ ials_status direct_epoch_enqueue(ials_ctx *c, Profiler *prof) {
 ials_status icd_epoch_enqueue(ials_ctx *c, Profiler *prof) {
     const int d = c->p.d;
     float *gH = c->icd_g, *gW = c->icd_g + d;
+    IALS_CUDA(icd_transpose(c, prof), "transposed factors");
     prof_mark(prof, K_GRAM, c->stream);
     IALS_CUDA(launch_gram(c->H, c->n_items, d, 0, 1, gH, c->gram_ws, c->stream), "Gramian column");
     prof_mark(prof, -1, c->stream);
@@ -368,6 +382,7 @@ ials_status icd_epoch_enqueue(ials_ctx *c, Profiler *prof) {
 
 ials_status step_enqueue(ials_ctx *c, int side, int block, Profiler *prof = nullptr) {
     if (use_icd(c)) {  // one coordinate: its Gramian column of the fixed side, then the pass
+        IALS_CUDA(icd_transpose(c, prof), "transposed factors");
         const float *F = side == 0 ? c->H : c->W;
         const int64_t n_fixed = side == 0 ? c->n_items : c->n_users;
         prof_mark(prof, K_GRAM, c->stream);
@@ -639,8 +654,10 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     if (b == 1) {
         ALLOC(c->icd_g, 2 * (int64_t)d, "Gramian columns");
         ALLOC(c->icd_gpart, (int64_t)(icd_row_grid(std::max(c->side[0].n_tasks, c->side[1].n_tasks), d) +
-                                      icd_split_grid(max_split)) * d,
+                                      icd_split_grid(max_split, d)) * d,
               "Gramian column partials");
+        ALLOC(c->WT, (int64_t)n_users * d, "W transposed");
+        ALLOC(c->HT, (int64_t)n_items * d, "H transposed");
         ALLOC(c->icd_done, 1, "completion counter");
     }
     ALLOC(c->g64a, (int64_t)d * d, "FP64 Gramian");

@@ -130,9 +130,14 @@ struct IcdArgs {
     float *gpart;        // partial columns: icd_row_grid blocks, then icd_split_grid blocks (d each)
     int32_t *done;       // completion counter of the final reduction (0 between passes)
     int32_t grid;        // blocks of the row kernel: icd_row_grid(n_tasks, d)
+    const float *FT;     // fixed side transposed, d x n_fixed
+    float *XT;           // updated side transposed, d x n_rows (kept current)
+    int64_t n_fixed;
 };
 int32_t icd_row_grid(int32_t n_tasks, int32_t d);
-int32_t icd_split_grid(int32_t n_split);
+int32_t icd_split_grid(int32_t n_split, int32_t d);
+// X (n x d) -> XT (d x n)
+cudaError_t launch_transpose(const float *X, int64_t n, int32_t d, float *XT, cudaStream_t s);
 cudaError_t launch_icd(const IcdArgs &a, cudaStream_t s);
 // Kernel attributes of the iCD kernels; call once outside any stream capture.
 cudaError_t icd_prepare();

@@ -18,6 +18,12 @@
 // path): the row kernel stores each chunk's two partial sums; a split kernel
 // sums them in chunk order, solves and applies; a residual kernel updates the
 // residuals of the long rows' pieces.
+//
+// Layout: the pass reads f_{c,f} from a transposed copy of the fixed side
+// (d x n, column f contiguous), which the epoch forms once and every pass keeps
+// current by writing x_{r,f} into the updated side's transposed copy as well.
+// The coordinate column of H (80 KB at 20,000 items) then stays in L1, and a
+// gathered 32-byte sector carries eight useful values instead of one.
 #include "ials_internal.cuh"
 
 #include <algorithm>
@@ -26,7 +32,10 @@ namespace ials {
 
 namespace {
 
-constexpr int kIcdWarps = 8;
+// warps per block of the row and split kernels: one block per SM; fewer warps
+// when d is large (each warp keeps a d-float partial column in shared memory)
+__host__ __device__ constexpr int icd_warps(int d) { return d <= 1024 ? 32 : 8; }
+constexpr int kIcdMaxWarps = 32;
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -83,11 +92,30 @@ __device__ __forceinline__ void last_block_reduce(const IcdArgs &a, int npart) {
     __syncthreads();
     if (!last) return;
     __threadfence();
-    const int d = a.s.d;
-    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+    // every thread sums a contiguous range of partials for one entry (so the
+    // loads are independent and in flight together); the ranges' sums are then
+    // added in range order, which fixes the summation order
+    extern __shared__ float4 smem4[];
+    float *red = reinterpret_cast<float *>(smem4);  // reuses the kernel's shared memory
+    const int d = a.s.d, nt = blockDim.x;
+    const int per_k = nt >= d ? nt / d : 1;           // threads per entry
+    const int span = (npart + per_k - 1) / per_k;
+    __syncthreads();
+    for (int k0 = 0; k0 < d; k0 += nt / per_k) {
+        const int k = k0 + threadIdx.x / per_k, h = threadIdx.x % per_k;
         float t = 0.f;
-        for (int p = 0; p < npart; ++p) t += __ldcg(a.gpart + (int64_t)p * d + k);
-        a.g_out[k] = t;
+        if (k < d && threadIdx.x < per_k * (nt / per_k)) {
+            const int p0 = h * span, p1 = min(npart, p0 + span);
+            for (int p = p0; p < p1; ++p) t += __ldcg(a.gpart + (int64_t)p * d + k);
+        }
+        red[threadIdx.x] = t;
+        __syncthreads();
+        if (h == 0 && k < d && threadIdx.x < per_k * (nt / per_k)) {
+            float u = 0.f;
+            for (int q = 0; q < per_k; ++q) u += red[threadIdx.x + q];
+            a.g_out[k] = u;
+        }
+        __syncthreads();
     }
     if (threadIdx.x == 0) *a.done = 0;
 }
@@ -95,42 +123,58 @@ __device__ __forceinline__ void last_block_reduce(const IcdArgs &a, int npart) {
 // Per task: the coordinate-f statistics of a row (or of a chunk of a long row,
 // stored to its slot), then for whole rows the update, the residual update and
 // the Gramian contribution.  Shared: g (d), one partial column per warp (d each).
+// Interactions are visited 64 at a time (two per lane) so that the dependent
+// loads of two gathers are in flight together.
 template <bool PERM, bool HAS_A>
-__global__ void __launch_bounds__(32 * kIcdWarps) k_icd_rows(const IcdArgs a) {
+__global__ void __launch_bounds__(32 * kIcdMaxWarps) k_icd_rows(const IcdArgs a) {
     extern __shared__ float4 smem4[];
     float *g = reinterpret_cast<float *>(smem4);
-    const int d = a.s.d, f = a.f, fn = a.fn;
-    float *wpart = g + d + (threadIdx.x >> 5) * d;
+    const int d = a.s.d, f = a.f, fn = a.fn, nw = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *wpart = g + d + warp * d;
     for (int k = threadIdx.x; k < d; k += blockDim.x) g[k] = a.g_in[k];
     for (int k = lane; k < d; k += 32) wpart[k] = 0.f;
     __syncthreads();
     const StepArgs &s = a.s;
+    const float *__restrict__ Ff = a.FT + (int64_t)f * a.n_fixed;  // column f of the fixed side
     const float gf = g[f];
-    const int nwarps = gridDim.x * kIcdWarps;
-    for (int t = blockIdx.x * kIcdWarps + warp; t < s.n_tasks; t += nwarps) {
+    const int nwarps = gridDim.x * nw;
+    for (int t = blockIdx.x * nw + warp; t < s.n_tasks; t += nwarps) {
         const Task tk = s.tasks[t];
         float num = 0.f, den = 0.f;
-        constexpr int KEEP = 4;  // interactions kept in registers for the residual update: 32 * KEEP
-        int qk[KEEP];
-        float fk[KEEP];
-        for (int j = 0; j * 32 < tk.len; ++j) {
-            const int i = j * 32 + lane;
-            int q = -1;
-            float fc = 0.f;
-            if (i < tk.len) {
-                const int64_t p = tk.begin + i;
-                q = PERM ? s.pos[p] : (int)p;
-                fc = s.F[(int64_t)s.idx[p] * d + f];
-                const float al = HAS_A ? s.alpha[q] : 1.f;
-                num = fmaf(al * s.e[q], fc, num);
-                den = fmaf(al * fc, fc, den);
-            }
-            if (j < KEEP) {
+        constexpr int KEEP = 2;  // 64-interaction rounds kept in registers for the residual update
+        int qk[KEEP][2];
+        float fk[KEEP][2];
+        for (int j = 0; j * 64 < tk.len; ++j) {
+            int q[2] = {-1, -1};
+            float fc[2] = {0.f, 0.f}, ev[2] = {0.f, 0.f}, al[2] = {1.f, 1.f};
 #pragma unroll
-                for (int u = 0; u < KEEP; ++u)
-                    if (u == j) { qk[u] = q; fk[u] = fc; }
+            for (int h = 0; h < 2; ++h) {
+                const int i = j * 64 + h * 32 + lane;
+                if (i < tk.len) {
+                    const int64_t p = tk.begin + i;
+                    q[h] = PERM ? s.pos[p] : (int)p;
+                    fc[h] = Ff[s.idx[p]];
+                }
             }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (q[h] >= 0) {
+                    ev[h] = s.e[q[h]];
+                    if (HAS_A) al[h] = s.alpha[q[h]];
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                num = fmaf(al[h] * ev[h], fc[h], num);
+                den = fmaf(al[h] * fc[h], fc[h], den);
+            }
+#pragma unroll
+            for (int u = 0; u < KEEP; ++u)
+                if (u == j) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) { qk[u][h] = q[h]; fk[u][h] = fc[h]; }
+                }
         }
         num = warp_sum(num);
         den = warp_sum(den);
@@ -159,20 +203,29 @@ __global__ void __launch_bounds__(32 * kIcdWarps) k_icd_rows(const IcdArgs a) {
             add_row(wpart, x, d, f, xf_new, coef, lane);
         }
         __syncwarp();
-        if (lane == 0) x[f] = xf_new;
-        for (int j = 0; j * 32 < tk.len; ++j) {
-            const int i = j * 32 + lane;
+        if (lane == 0) {
+            x[f] = xf_new;
+            a.XT[(int64_t)f * s.n_rows + tk.row] = xf_new;
+        }
+        for (int j = 0; j * 64 < tk.len; ++j) {
             if (j < KEEP) {
-                int q = -1;
-                float fc = 0.f;
 #pragma unroll
                 for (int u = 0; u < KEEP; ++u)
-                    if (u == j) { q = qk[u]; fc = fk[u]; }
-                if (q >= 0) s.e[q] = fmaf(-delta, fc, s.e[q]);
-            } else if (i < tk.len) {
-                const int64_t p = tk.begin + i;
-                const int q = PERM ? s.pos[p] : (int)p;
-                s.e[q] = fmaf(-delta, s.F[(int64_t)s.idx[p] * d + f], s.e[q]);
+                    if (u == j) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+                            if (qk[u][h] >= 0) s.e[qk[u][h]] = fmaf(-delta, fk[u][h], s.e[qk[u][h]]);
+                    }
+            } else {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = j * 64 + h * 32 + lane;
+                    if (i < tk.len) {
+                        const int64_t p = tk.begin + i;
+                        const int q = PERM ? s.pos[p] : (int)p;
+                        s.e[q] = fmaf(-delta, Ff[s.idx[p]], s.e[q]);
+                    }
+                }
             }
         }
     }
@@ -181,7 +234,7 @@ __global__ void __launch_bounds__(32 * kIcdWarps) k_icd_rows(const IcdArgs a) {
     // warp partials in warp order -> this block's partial column
     for (int k = threadIdx.x; k < d; k += blockDim.x) {
         float t = 0.f;
-        for (int w = 0; w < kIcdWarps; ++w) t += g[d + w * d + k];
+        for (int w = 0; w < nw; ++w) t += g[d + w * d + k];
         a.gpart[(int64_t)blockIdx.x * d + k] = t;
     }
     if (s.n_split == 0) last_block_reduce(a, gridDim.x);
@@ -191,10 +244,10 @@ __global__ void __launch_bounds__(32 * kIcdWarps) k_icd_rows(const IcdArgs a) {
 // forms the dense terms and the update, applies it and records delta; each
 // block sums its rows' Gramian contributions in row order into one partial
 // column (after the row kernel's), and the last block reduces all partials.
-__global__ void __launch_bounds__(32 * kIcdWarps) k_icd_split(const IcdArgs a) {
+__global__ void __launch_bounds__(32 * kIcdMaxWarps) k_icd_split(const IcdArgs a) {
     extern __shared__ float4 smem4[];
     float *g = reinterpret_cast<float *>(smem4);
-    const int d = a.s.d, f = a.f, fn = a.fn;
+    const int d = a.s.d, f = a.f, fn = a.fn, kIcdWarps = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *wpart = g + d + warp * d;
     for (int k = threadIdx.x; k < d; k += blockDim.x) g[k] = a.g_in[k];
@@ -226,6 +279,7 @@ __global__ void __launch_bounds__(32 * kIcdWarps) k_icd_split(const IcdArgs a) {
         __syncwarp();
         if (lane == 0) {
             x[f] = xf_new;
+            a.XT[(int64_t)f * s.n_rows + sr.row] = xf_new;
             s.delta[i] = delta;
         }
     }
@@ -245,29 +299,48 @@ __global__ void __launch_bounds__(256) k_icd_split_resid(const IcdArgs a) {
     const StepArgs &s = a.s;
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const float *__restrict__ Ff = a.FT + (int64_t)a.f * a.n_fixed;
     for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < s.n_stasks; t += nwarps) {
         const Task tk = s.stasks[t];
         const float delta = s.delta[tk.srow];
-        for (int i = lane; i < tk.len; i += 32) {
-            const int64_t p = tk.begin + i;
-            const int q = PERM ? s.pos[p] : (int)p;
-            s.e[q] = fmaf(-delta, s.F[(int64_t)s.idx[p] * s.d + a.f], s.e[q]);
+        // a piece holds at most 128 interactions: four per lane, all loads issued first
+        int q[4];
+        float fc[4], ev[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = lane + 32 * u;
+            q[u] = -1;
+            if (i < tk.len) {
+                const int64_t p = tk.begin + i;
+                q[u] = PERM ? s.pos[p] : (int)p;
+                fc[u] = Ff[s.idx[p]];
+            }
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (q[u] >= 0) ev[u] = s.e[q[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (q[u] >= 0) s.e[q[u]] = fmaf(-delta, fc[u], ev[u]);
     }
 }
 
-constexpr int kIcdMaxSmem = (int)(sizeof(float) * 4096 * (1 + kIcdWarps));  // d <= 4096
+// g and the warps' partial columns: d (1 + warps) floats, at most 4096 x 9
+constexpr int kIcdMaxSmem = (int)(sizeof(float) * 4096 * (1 + 8));
+static_assert(1024 * (1 + 32) <= 4096 * (1 + 8), "shared-memory bound of the largest d per warp count");
 
 template <bool PERM, bool HAS_A>
 cudaError_t launch_icd_t(const IcdArgs &a0, cudaStream_t st) {
     IcdArgs a = a0;
-    const size_t smem = sizeof(float) * (size_t)a.s.d * (1 + kIcdWarps);
+    const int kIcdWarps = icd_warps(a.s.d);
+    // g and the warps' partial columns; at least one float per thread for the final reduction
+    const size_t smem = sizeof(float) * std::max<size_t>((size_t)a.s.d * (1 + kIcdWarps), 32 * kIcdWarps);
     prof_mark(a.s.prof, K_SPARSE, st);
     k_icd_rows<PERM, HAS_A><<<a.grid, 32 * kIcdWarps, smem, st>>>(a);
     prof_mark(a.s.prof, -1, st);
     if (a.s.n_split > 0) {
         prof_mark(a.s.prof, K_SPLIT_SOLVE, st);
-        k_icd_split<<<icd_split_grid(a.s.n_split), 32 * kIcdWarps, smem, st>>>(a);
+        k_icd_split<<<icd_split_grid(a.s.n_split, a.s.d), 32 * kIcdWarps, smem, st>>>(a);
         prof_mark(a.s.prof, K_SPLIT_RESID, st);
         const int g3 = (int)std::min<int64_t>((a.s.n_stasks + 7) / 8, 152 * 8);
         k_icd_split_resid<PERM><<<g3 > 0 ? g3 : 1, 256, 0, st>>>(a);
@@ -279,19 +352,42 @@ cudaError_t launch_icd_t(const IcdArgs &a0, cudaStream_t st) {
 }  // namespace
 
 int32_t icd_row_grid(int32_t n_tasks, int32_t d) {
-    // one block per SM (two when d is small enough for the shared partials), never
-    // more blocks than eight-task groups
-    const int per_sm = d <= 2048 ? 2 : 1;
-    int32_t g = 152 * per_sm;
-    const int32_t need = (n_tasks + kIcdWarps - 1) / kIcdWarps;
+    // one block per SM, never more blocks than warp-sized task groups need
+    int32_t g = 152;
+    const int32_t need = (n_tasks + icd_warps(d) - 1) / icd_warps(d);
     if (g > need) g = need;
     return g > 0 ? g : 1;
 }
 
-int32_t icd_split_grid(int32_t n_split) {
-    int32_t g = (n_split + kIcdWarps - 1) / kIcdWarps;
+int32_t icd_split_grid(int32_t n_split, int32_t d) {
+    int32_t g = (n_split + icd_warps(d) - 1) / icd_warps(d);
     if (g > 38) g = 38;
     return g > 0 ? g : 1;
+}
+
+// X (n x d, row-major) -> XT (d x n), 32 x 32 tiles through shared memory.
+__global__ void k_transpose(const float *__restrict__ X, int64_t n, int32_t d, float *__restrict__ XT) {
+    __shared__ float tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i;
+        const int c = c0 + threadIdx.x;
+        if (r < n && c < d) tile[i][threadIdx.x] = X[r * d + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i;
+        const int64_t r = r0 + threadIdx.x;
+        if (r < n && c < d) XT[(int64_t)c * n + r] = tile[threadIdx.x][i];
+    }
+}
+
+cudaError_t launch_transpose(const float *X, int64_t n, int32_t d, float *XT, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((d + 31) / 32));
+    k_transpose<<<grid, dim3(32, 8), 0, s>>>(X, n, d, XT);
+    return cudaGetLastError();
 }
 
 cudaError_t icd_prepare() {
