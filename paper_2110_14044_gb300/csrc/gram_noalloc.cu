@@ -84,6 +84,13 @@ extern "C" ials_status ials_partial_gramian_noalloc(const float *X, int64_t n, i
                 return IALS_ECUDA;
             }
             g_scratch_ptr[dev] = static_cast<float *>(p);
+            e = ials::dense_prepare();  // kernel attributes, also once per device before any capture
+            if (e != cudaSuccess) {
+                ials::set_last_error(std::string("kernel attributes: ") + cudaGetErrorString(e));
+                cudaGetLastError();
+                g_scratch_ptr[dev] = nullptr;
+                return IALS_ECUDA;
+            }
         }
         ws = g_scratch_ptr[dev];
     }

@@ -145,6 +145,8 @@ struct ials_ctx {
     // iCD path (b = 1): Gramian columns (two of d), their partials, completion counter
     float *icd_g = nullptr, *icd_gpart = nullptr;
     float *WT = nullptr, *HT = nullptr;  // transposed factors (d x n), kept current by the passes
+    float *e_i = nullptr, *alpha_i = nullptr;  // item-major residual copy and weights
+    float *dU = nullptr, *dI = nullptr, *icd_xold = nullptr;  // per-row deltas of the last passes
     int32_t *icd_done = nullptr;
     cudaGraphExec_t graph = nullptr;
     bool own_stream = false;
@@ -308,11 +310,19 @@ cudaError_t icd_transpose(ials_ctx *c, Profiler *prof) {
 }
 
 // One iCD pass: side `side`, coordinate f, fixed-side Gramian column in g_in;
-// forms the updated side's column fn (>= 0) into g_out on the way.
+// forms the updated side's column fn (>= 0) into g_out on the way.  The side's
+// own residual copy must be current except for the previous pass's deltas
+// when `pending` (user pass: the item pass at f - 1; item pass: the user pass at f).
 ials_status icd_pass_enqueue(ials_ctx *c, int side, int f, int fn, const float *g_in, float *g_out,
-                             Profiler *prof) {
+                             bool pending, Profiler *prof) {
     IcdArgs a;
     a.s = step_args(c, side, f, prof);
+    a.eo = side == 0 ? c->e : c->e_i;
+    a.alpha_o = side == 0 ? c->alpha : c->alpha_i;
+    a.dprev = pending ? (side == 0 ? c->dI : c->dU) : nullptr;
+    a.fprev = side == 0 ? f - 1 : f;
+    a.dself = side == 0 ? c->dU : c->dI;
+    a.xold = c->icd_xold;
     a.f = f;
     a.fn = fn;
     a.g_in = g_in;
@@ -368,13 +378,15 @@ ials_status icd_epoch_enqueue(ials_ctx *c, Profiler *prof) {
     const int d = c->p.d;
     float *gH = c->icd_g, *gW = c->icd_g + d;
     IALS_CUDA(icd_transpose(c, prof), "transposed factors");
+    prof_mark(prof, K_RESIDUAL, c->stream);
+    IALS_CUDA(launch_perm_gather(c->e, c->side[1].pos, c->nnz, c->e_i, c->stream), "item-major residuals");
     prof_mark(prof, K_GRAM, c->stream);
     IALS_CUDA(launch_gram(c->H, c->n_items, d, 0, 1, gH, c->gram_ws, c->stream), "Gramian column");
     prof_mark(prof, -1, c->stream);
     for (int f = 0; f < d; ++f) {
-        ials_status st = icd_pass_enqueue(c, 0, f, f, gH, gW, prof);
+        ials_status st = icd_pass_enqueue(c, 0, f, f, gH, gW, f > 0, prof);
         if (st != IALS_OK) return st;
-        st = icd_pass_enqueue(c, 1, f, f + 1 < d ? f + 1 : -1, gW, gH, prof);
+        st = icd_pass_enqueue(c, 1, f, f + 1 < d ? f + 1 : -1, gW, gH, true, prof);
         if (st != IALS_OK) return st;
     }
     return IALS_OK;
@@ -388,7 +400,13 @@ ials_status step_enqueue(ials_ctx *c, int side, int block, Profiler *prof = null
         prof_mark(prof, K_GRAM, c->stream);
         IALS_CUDA(launch_gram(F, n_fixed, c->p.d, block, 1, c->icd_g, c->gram_ws, c->stream), "Gramian column");
         prof_mark(prof, -1, c->stream);
-        return icd_pass_enqueue(c, side, block, -1, c->icd_g, nullptr, prof);
+        if (side == 0) return icd_pass_enqueue(c, 0, block, -1, c->icd_g, nullptr, false, prof);
+        // the item pass on an item-major copy of the (current) user-major cache, written back
+        IALS_CUDA(launch_perm_gather(c->e, c->side[1].pos, c->nnz, c->e_i, c->stream), "item-major residuals");
+        ials_status st = icd_pass_enqueue(c, 1, block, -1, c->icd_g, nullptr, false, prof);
+        if (st != IALS_OK) return st;
+        IALS_CUDA(launch_perm_scatter(c->e_i, c->side[1].pos, c->nnz, c->e, c->stream), "user-major residuals");
+        return IALS_OK;
     }
     const int32_t d = c->p.d, b = c->p.b, p0 = block * b;
     SideDev &sd = c->side[side];
@@ -658,6 +676,11 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
               "Gramian column partials");
         ALLOC(c->WT, (int64_t)n_users * d, "W transposed");
         ALLOC(c->HT, (int64_t)n_items * d, "H transposed");
+        ALLOC(c->e_i, nnz, "item-major residuals");
+        if (alpha) ALLOC(c->alpha_i, nnz, "item-major weights");
+        ALLOC(c->dU, n_users, "user deltas");
+        ALLOC(c->dI, n_items, "item deltas");
+        ALLOC(c->icd_xold, max_split, "long-row coordinates");
         ALLOC(c->icd_done, 1, "completion counter");
     }
     ALLOC(c->g64a, (int64_t)d * d, "FP64 Gramian");
@@ -683,6 +706,10 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
         up(ht[sd].stasks.data(), c->side[sd].stasks, sizeof(Task) * ht[sd].stasks.size(), "split tasks");
     }
     if (us != IALS_OK) { delete c; return us; }
+    if (c->alpha_i) {
+        const cudaError_t ge = launch_perm_gather(c->alpha, c->side[1].pos, nnz, c->alpha_i, c->stream);
+        if (ge != cudaSuccess) { delete c; return cuda_fail(ge, "item-major weights"); }
+    }
     cudaError_t e1 = launch_init_normal(c->W, (int64_t)n_users * d, p.init_std, p.seed, 1, c->stream);
     cudaError_t e2 = launch_init_normal(c->H, (int64_t)n_items * d, p.init_std, p.seed, 2, c->stream);
     cudaError_t e3 = cudaMemsetAsync(c->stats, 0, 2 * sizeof(int64_t), c->stream);
@@ -719,6 +746,7 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
         }
     }
     if (e7 == cudaSuccess && b == 1) e7 = icd_prepare();
+    if (e7 == cudaSuccess) e7 = dense_prepare();
     cudaError_t e8 = cudaStreamSynchronize(c->stream);
     for (cudaError_t e : {e1, e2, e3, e4, e5, e6, e7, e8})
         if (e != cudaSuccess) { delete c; return cuda_fail(e, "context initialisation"); }
@@ -755,8 +783,9 @@ ials_status ials_epoch(ials_ctx *c, int32_t n_epochs, double *objective_after) {
             if (st != IALS_OK) return st;
         }
     }
-    // each epoch recomputed the cache first; the iALS path keeps none
-    if (n_epochs > 0) c->e_stale = use_ials(c);
+    // each epoch recomputed the cache first; the iALS path keeps none, and the iCD
+    // path leaves the user-major copy one item pass behind
+    if (n_epochs > 0) c->e_stale = use_ials(c) || use_icd(c);
     ials_status st = finish(c);
     if (objective_after && (st == IALS_OK || st == IALS_ENOTPD)) {
         ials_status s2 = objective_enqueue(c);
@@ -846,7 +875,7 @@ ials_status ials_profile_epochs(ials_ctx *c, int32_t n_epochs, double *kernel_ms
         ials_status st = epoch_enqueue(c, &prof);
         if (st != IALS_OK) return st;
     }
-    if (n_epochs > 0) c->e_stale = use_ials(c);
+    if (n_epochs > 0) c->e_stale = use_ials(c) || use_icd(c);
     prof_mark(&prof, -1, c->stream);
     ials_status st = finish(c);
     if (st != IALS_OK && st != IALS_ENOTPD) return st;
@@ -945,6 +974,7 @@ ials_status ials_partial_gramian(const float *X, int64_t n, int32_t d, int32_t p
     if (!X || !G || n < 0 || d < 1 || bs < 1 || p0 < 0 || p0 + bs > d)
         return fail(IALS_EINVAL, "bad Gramian arguments");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    IALS_CUDA(dense_prepare(), "kernel attributes");
     float *ws = nullptr;
     const int64_t wsn = gram_ws_floats(n, d, bs);
     if (cudaMalloc(&ws, sizeof(float) * (size_t)std::max<int64_t>(wsn, 1)) != cudaSuccess) {

@@ -133,11 +133,20 @@ struct IcdArgs {
     const float *FT;     // fixed side transposed, d x n_fixed
     float *XT;           // updated side transposed, d x n_rows (kept current)
     int64_t n_fixed;
+    float *eo;           // residuals in this side's CSR order
+    const float *alpha_o;  // weights in this side's CSR order, or nullptr
+    const float *dprev;  // deltas of the previous pass (other side, by column id), or nullptr
+    int32_t fprev;       // coordinate of the updated row that dprev multiplies
+    float *dself;        // this pass's delta per row (n_rows)
+    float *xold;         // long rows: the fprev coordinate before the update (n_split)
 };
 int32_t icd_row_grid(int32_t n_tasks, int32_t d);
 int32_t icd_split_grid(int32_t n_split, int32_t d);
 // X (n x d) -> XT (d x n)
 cudaError_t launch_transpose(const float *X, int64_t n, int32_t d, float *XT, cudaStream_t s);
+// dst[t] = src[pos[t]] and dst[pos[t]] = src[t], t < n
+cudaError_t launch_perm_gather(const float *src, const int32_t *pos, int64_t n, float *dst, cudaStream_t s);
+cudaError_t launch_perm_scatter(const float *src, const int32_t *pos, int64_t n, float *dst, cudaStream_t s);
 cudaError_t launch_icd(const IcdArgs &a, cudaStream_t s);
 // Kernel attributes of the iCD kernels; call once outside any stream capture.
 cudaError_t icd_prepare();
@@ -181,6 +190,8 @@ cudaError_t launch_reg_loss(const int64_t *ptr, const float *X, int32_t n_rows, 
 cudaError_t launch_frobenius(const double *A, const double *B, int32_t n, double alpha0,
                              double *out, cudaStream_t s);
 
+// Kernel attributes of the dense kernels; call once outside any stream capture.
+cudaError_t dense_prepare();
 // Split-K partial Gramian G = X^T X[:, p0:p0+bs] (d x bs).
 // ws must hold gram_ws_floats(n, d, bs) floats.
 int64_t gram_ws_floats(int64_t n, int32_t d, int32_t bs);

@@ -308,6 +308,160 @@ __global__ void __launch_bounds__(256) k_gram_tile(const float *__restrict__ X, 
     }
 }
 
+// Large-d split-K Gramian (d % 512 == 0, bs % 32 == 0): 512 (coordinates) x 32
+// (block columns) output tile per block, 256 threads with 8 x 8 outputs each
+// (packed FP32 pairs), 16-row slabs of X staged by cp.async into two buffers so
+// the next slab loads while the current one is multiplied.  Partials as k_gram_tile.
+constexpr int GB_TM = 512, GB_TN = 32, GB_KS = 16;
+constexpr int GB_SMEM = 2 * GB_KS * (GB_TM + GB_TN) * 4;
+
+__device__ __forceinline__ void cp_async16_dense(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void fma2_dense(float &d0, float &d1, float a0, float a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rd, {%0, %1};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rd;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+__global__ void __launch_bounds__(256, 2) k_gram_big(const float *__restrict__ X, int64_t n, int32_t d,
+                                                     int32_t p0, int32_t bs, int64_t rows_per,
+                                                     float *__restrict__ ws) {
+    extern __shared__ float4 gsm4[];
+    float *As = reinterpret_cast<float *>(gsm4);          // [2][KS][TM]
+    float *Bs = As + 2 * GB_KS * GB_TM;                    // [2][KS][TN]
+    const int tid = threadIdx.x, tx = tid & 3, ty = tid >> 2;
+    const int m0 = blockIdx.x * GB_TM, n0 = blockIdx.y * GB_TN;
+    const int64_t k_beg = (int64_t)blockIdx.z * rows_per;
+    const int64_t k_end = min(n, k_beg + rows_per);
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    auto load = [&](int64_t k0, int bi) {
+        float *a = As + bi * GB_KS * GB_TM, *b = Bs + bi * GB_KS * GB_TN;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {  // 16 rows x 128 float4
+            const int f = tid + 256 * q, kk = f >> 7, v = f & 127;
+            const int64_t k = k0 + kk;
+            if (k < k_end) cp_async16_dense(a + kk * GB_TM + 4 * v, X + k * d + m0 + 4 * v);
+            else *reinterpret_cast<float4 *>(a + kk * GB_TM + 4 * v) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (tid < GB_KS * GB_TN / 4) {
+            const int kk = tid >> 3, v = tid & 7;
+            const int64_t k = k0 + kk;
+            if (k < k_end) cp_async16_dense(b + kk * GB_TN + 4 * v, X + k * d + p0 + n0 + 4 * v);
+            else *reinterpret_cast<float4 *>(b + kk * GB_TN + 4 * v) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    int bi = 0;
+    if (k_beg < k_end) load(k_beg, 0);
+    for (int64_t k0 = k_beg; k0 < k_end; k0 += GB_KS) {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+        if (k0 + GB_KS < k_end) load(k0 + GB_KS, bi ^ 1);
+        const float *a = As + bi * GB_KS * GB_TM + ty * 8, *b = Bs + bi * GB_KS * GB_TN + tx * 8;
+#pragma unroll
+        for (int kk = 0; kk < GB_KS; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(a + kk * GB_TM);
+            const float4 a1 = *reinterpret_cast<const float4 *>(a + kk * GB_TM + 4);
+            const float4 b0 = *reinterpret_cast<const float4 *>(b + kk * GB_TN);
+            const float4 b1 = *reinterpret_cast<const float4 *>(b + kk * GB_TN + 4);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) fma2_dense(acc[i][j], acc[i][j + 1], av[i], av[i], bv[j], bv[j + 1]);
+        }
+        bi ^= 1;
+    }
+    float *out = ws + (int64_t)blockIdx.z * d * bs;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int m = m0 + ty * 8 + i;
+        float4 *o = reinterpret_cast<float4 *>(out + (int64_t)m * bs + n0 + tx * 8);
+        o[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        o[1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    }
+}
+
+// Large-d row terms (d % 16 == 0, bs % 32 == 0): 256 rows x 32 block columns per
+// block, 256 threads with 8 rows x 4 columns each; X rows and G in 16-wide
+// k-slabs staged by cp.async into two buffers (rows padded to 20 floats).
+constexpr int RB_TM = 256, RB_TN = 32, RB_KS = 16, RB_SA = RB_KS + 4;
+
+__global__ void __launch_bounds__(256, 2) k_rowterm_big(const float *__restrict__ X,
+                                                        const int64_t *__restrict__ ptr, int32_t n_rows,
+                                                        int32_t d, int32_t p0, int32_t bs,
+                                                        const float *__restrict__ G, float alpha0,
+                                                        float lambda, float nu, float *__restrict__ R) {
+    __shared__ __align__(16) float As[2][RB_TM * RB_SA];
+    __shared__ __align__(16) float Bs[2][RB_KS * RB_TN];
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+    const int64_t r0 = (int64_t)blockIdx.x * RB_TM;
+    const int n0 = blockIdx.y * RB_TN;
+    float acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    auto load = [&](int k0, int bi) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {  // 256 rows x 4 float4
+            const int f = tid + 256 * q, rr = f >> 2, v = f & 3;
+            const int64_t r = r0 + rr;
+            float *dst = &As[bi][rr * RB_SA + 4 * v];
+            if (r < n_rows) cp_async16_dense(dst, X + r * d + k0 + 4 * v);
+            else *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (tid < RB_KS * RB_TN / 4) {
+            const int kk = tid >> 3, v = tid & 7;
+            cp_async16_dense(&Bs[bi][kk * RB_TN + 4 * v], G + (int64_t)(k0 + kk) * bs + n0 + 4 * v);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    int bi = 0;
+    load(0, 0);
+    for (int k0 = 0; k0 < d; k0 += RB_KS) {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+        if (k0 + RB_KS < d) load(k0 + RB_KS, bi ^ 1);
+#pragma unroll
+        for (int kq = 0; kq < RB_KS; kq += 4) {
+            float4 av[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) av[i] = *reinterpret_cast<const float4 *>(&As[bi][(ty * 8 + i) * RB_SA + kq]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 b = *reinterpret_cast<const float4 *>(&Bs[bi][(kq + k) * RB_TN + tx * 4]);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float a = k == 0 ? av[i].x : (k == 1 ? av[i].y : (k == 2 ? av[i].z : av[i].w));
+                    fma2_dense(acc[i][0], acc[i][1], a, a, b.x, b.y);
+                    fma2_dense(acc[i][2], acc[i][3], a, a, b.z, b.w);
+                }
+            }
+        }
+        bi ^= 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t r = r0 + ty * 8 + i;
+        if (r >= n_rows) continue;
+        const float lam = lambda * (1.0f + nu * (float)(ptr[r + 1] - ptr[r]));
+        const float4 x = *reinterpret_cast<const float4 *>(X + r * d + p0 + n0 + tx * 4);
+        *reinterpret_cast<float4 *>(R + r * bs + n0 + tx * 4) =
+            make_float4(alpha0 * acc[i][0] + lam * x.x, alpha0 * acc[i][1] + lam * x.y,
+                        alpha0 * acc[i][2] + lam * x.z, alpha0 * acc[i][3] + lam * x.w);
+    }
+}
+
 // Fixed-order reduction of the split-K partials.
 template <typename T>
 __global__ void k_gram_reduce(const T *__restrict__ ws, int32_t nsplit, int64_t count,
@@ -318,6 +472,18 @@ __global__ void k_gram_reduce(const T *__restrict__ ws, int32_t nsplit, int64_t 
     for (int s = 0; s < nsplit; ++s) t += ws[(int64_t)s * count + i];
     G[i] = t;
 }
+
+}  // namespace
+
+// Kernel attributes of the dense kernels (dynamic shared memory of the large-d
+// Gramian); call once outside any stream capture.
+cudaError_t dense_prepare() {
+    static cudaError_t done = cudaErrorNotReady;
+    if (done != cudaSuccess) done = cudaFuncSetAttribute(k_gram_big, cudaFuncAttributeMaxDynamicSharedMemorySize, GB_SMEM);
+    return done;
+}
+
+namespace {
 
 struct GramPlan {
     int tm_size, tn_size, tm, tn, nsplit;
@@ -330,9 +496,16 @@ inline void tile_shape(int32_t bs, int &TM, int &TN) {
     else { TM = 64; TN = 64; }
 }
 
-GramPlan gram_plan(int64_t n, int32_t d, int32_t bs) {
+// The large-d kernel's shapes (FP32 partial Gramians only).
+inline bool gram_big(int32_t d, int32_t bs) { return d % GB_TM == 0 && bs % GB_TN == 0; }
+
+GramPlan gram_plan(int64_t n, int32_t d, int32_t bs, bool allow_big = true) {
     GramPlan p;
     tile_shape(bs, p.tm_size, p.tn_size);
+    if (allow_big && gram_big(d, bs)) {
+        p.tm_size = GB_TM;
+        p.tn_size = GB_TN;
+    }
     p.tm = (d + p.tm_size - 1) / p.tm_size;
     p.tn = (bs + p.tn_size - 1) / p.tn_size;
     const int64_t tiles = (int64_t)p.tm * p.tn;
@@ -351,6 +524,11 @@ template <bool F64>
 void launch_gram_tiles(const GramPlan &p, const float *X, int64_t n, int32_t d, int32_t p0,
                        int32_t bs, void *ws, cudaStream_t s) {
     const dim3 grid(p.tm, p.tn, p.nsplit);
+    if (!F64 && p.tm_size == GB_TM) {
+        dense_prepare();  // a no-op after the first call (made at context creation)
+        k_gram_big<<<grid, 256, GB_SMEM, s>>>(X, n, d, p0, bs, p.rows_per, static_cast<float *>(ws));
+        return;
+    }
     if (p.tn_size == 16) k_gram_tile<256, 16, F64><<<grid, 256, 0, s>>>(X, n, d, p0, bs, p.rows_per, ws);
     else if (p.tn_size == 32) k_gram_tile<128, 32, F64><<<grid, 256, 0, s>>>(X, n, d, p0, bs, p.rows_per, ws);
     else k_gram_tile<64, 64, F64><<<grid, 256, 0, s>>>(X, n, d, p0, bs, p.rows_per, ws);
@@ -616,7 +794,7 @@ cudaError_t launch_gram_reduce_cols(const float *ws, int nsplit, int32_t rows, i
 }
 
 int64_t gram64_ws_doubles(int64_t n, int32_t d) {
-    GramPlan p = gram_plan(n, d, d);
+    GramPlan p = gram_plan(n, d, d, false);
     return (int64_t)p.nsplit * d * d;
 }
 
@@ -624,7 +802,7 @@ cudaError_t launch_gram64(const float *X, int64_t n, int32_t d, double *G64, dou
                           cudaStream_t s) {
     const int64_t count = (int64_t)d * d;
     if (n == 0) return cudaMemsetAsync(G64, 0, sizeof(double) * count, s);
-    GramPlan p = gram_plan(n, d, d);
+    GramPlan p = gram_plan(n, d, d, false);
     launch_gram_tiles<true>(p, X, n, d, 0, d, ws, s);
     k_gram_reduce<double><<<(unsigned)((count + 255) / 256), 256, 0, s>>>(ws, p.nsplit, count, G64);
     return cudaGetLastError();
@@ -634,6 +812,11 @@ cudaError_t launch_rowterm(const float *X, const int64_t *ptr, int32_t n_rows, i
                            int32_t p0, int32_t bs, const float *G, float alpha0, float lambda,
                            float nu, float *R, cudaStream_t s) {
     if (n_rows == 0) return cudaSuccess;
+    if (d % RB_KS == 0 && bs % RB_TN == 0) {
+        const dim3 grid((unsigned)((n_rows + RB_TM - 1) / RB_TM), bs / RB_TN);
+        k_rowterm_big<<<grid, 256, 0, s>>>(X, ptr, n_rows, d, p0, bs, G, alpha0, lambda, nu, R);
+        return cudaGetLastError();
+    }
     int TM, TN;
     tile_shape(bs, TM, TN);
     dim3 grid((n_rows + TM - 1) / TM, (bs + TN - 1) / TN);

@@ -19,6 +19,16 @@
 // sums them in chunk order, solves and applies; a residual kernel updates the
 // residuals of the long rows' pieces.
 //
+// Residuals: each side keeps its own copy of the residual cache in its own CSR
+// order (users: user-major, items: item-major), so every pass reads and writes
+// its residuals contiguously instead of through the position map.  A pass
+// changes one coordinate per row, so its effect on the other side's copy is
+// one scalar per row: the item pass at f lowers e(u,i) by delta_i w_{u,f}, and
+// the next user pass applies that on the fly as it reads its copy,
+// e(u,i) - delta_i^{prev} w_{u,f} (and the item pass applies the user pass's
+// delta_u h_{i,f} likewise).  Each copy is thus exact whenever its side reads
+// it; the user-major cache is rebuilt before anything else reads it.
+//
 // Layout: the pass reads f_{c,f} from a transposed copy of the fixed side
 // (d x n, column f contiguous), which the epoch forms once and every pass keeps
 // current by writing x_{r,f} into the updated side's transposed copy as well.
@@ -125,7 +135,7 @@ __device__ __forceinline__ void last_block_reduce(const IcdArgs &a, int npart) {
 // the Gramian contribution.  Shared: g (d), one partial column per warp (d each).
 // Interactions are visited 64 at a time (two per lane) so that the dependent
 // loads of two gathers are in flight together.
-template <bool PERM, bool HAS_A>
+template <bool HAS_A, bool DPREV>
 __global__ void __launch_bounds__(32 * kIcdMaxWarps) k_icd_rows(const IcdArgs a) {
     extern __shared__ float4 smem4[];
     float *g = reinterpret_cast<float *>(smem4);
@@ -137,35 +147,33 @@ __global__ void __launch_bounds__(32 * kIcdMaxWarps) k_icd_rows(const IcdArgs a)
     __syncthreads();
     const StepArgs &s = a.s;
     const float *__restrict__ Ff = a.FT + (int64_t)f * a.n_fixed;  // column f of the fixed side
+    float *__restrict__ eo = a.eo;
     const float gf = g[f];
     const int nwarps = gridDim.x * nw;
     for (int t = blockIdx.x * nw + warp; t < s.n_tasks; t += nwarps) {
         const Task tk = s.tasks[t];
+        float *x = s.X + (int64_t)tk.row * d;
+        const float xp = DPREV ? x[a.fprev] : 0.f;  // this row's coordinate the previous pass's deltas multiply
         float num = 0.f, den = 0.f;
         constexpr int KEEP = 2;  // 64-interaction rounds kept in registers for the residual update
-        int qk[KEEP][2];
-        float fk[KEEP][2];
+        float ek[KEEP][2], fk[KEEP][2];
         for (int j = 0; j * 64 < tk.len; ++j) {
-            int q[2] = {-1, -1};
-            float fc[2] = {0.f, 0.f}, ev[2] = {0.f, 0.f}, al[2] = {1.f, 1.f};
+            float fc[2] = {0.f, 0.f}, ev[2] = {0.f, 0.f}, al[2] = {1.f, 1.f}, dp[2] = {0.f, 0.f};
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int i = j * 64 + h * 32 + lane;
                 if (i < tk.len) {
                     const int64_t p = tk.begin + i;
-                    q[h] = PERM ? s.pos[p] : (int)p;
-                    fc[h] = Ff[s.idx[p]];
+                    const int c = s.idx[p];
+                    fc[h] = Ff[c];
+                    ev[h] = eo[p];
+                    if (DPREV) dp[h] = a.dprev[c];
+                    if (HAS_A) al[h] = a.alpha_o[p];
                 }
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                if (q[h] >= 0) {
-                    ev[h] = s.e[q[h]];
-                    if (HAS_A) al[h] = s.alpha[q[h]];
-                }
-            }
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
+                if (DPREV) ev[h] = fmaf(-dp[h], xp, ev[h]);
                 num = fmaf(al[h] * ev[h], fc[h], num);
                 den = fmaf(al[h] * fc[h], fc[h], den);
             }
@@ -173,7 +181,7 @@ __global__ void __launch_bounds__(32 * kIcdMaxWarps) k_icd_rows(const IcdArgs a)
             for (int u = 0; u < KEEP; ++u)
                 if (u == j) {
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) { qk[u][h] = q[h]; fk[u][h] = fc[h]; }
+                    for (int h = 0; h < 2; ++h) { ek[u][h] = ev[h]; fk[u][h] = fc[h]; }
                 }
         }
         num = warp_sum(num);
@@ -185,7 +193,6 @@ __global__ void __launch_bounds__(32 * kIcdMaxWarps) k_icd_rows(const IcdArgs a)
             }
             continue;
         }
-        float *x = s.X + (int64_t)tk.row * d;
         const float lam = s.lambda * (1.0f + s.nu * (float)tk.len);
         const float dot = row_dot(x, g, d, lane);
         const float xf = x[f];
@@ -206,26 +213,28 @@ __global__ void __launch_bounds__(32 * kIcdMaxWarps) k_icd_rows(const IcdArgs a)
         if (lane == 0) {
             x[f] = xf_new;
             a.XT[(int64_t)f * s.n_rows + tk.row] = xf_new;
+            a.dself[tk.row] = delta;
         }
         for (int j = 0; j * 64 < tk.len; ++j) {
-            if (j < KEEP) {
 #pragma unroll
-                for (int u = 0; u < KEEP; ++u)
-                    if (u == j) {
+            for (int h = 0; h < 2; ++h) {
+                const int i = j * 64 + h * 32 + lane;
+                if (i >= tk.len) continue;
+                const int64_t p = tk.begin + i;
+                float ev, fc;
+                if (j < KEEP) {
+                    ev = 0.f;
+                    fc = 0.f;
 #pragma unroll
-                        for (int h = 0; h < 2; ++h)
-                            if (qk[u][h] >= 0) s.e[qk[u][h]] = fmaf(-delta, fk[u][h], s.e[qk[u][h]]);
-                    }
-            } else {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int i = j * 64 + h * 32 + lane;
-                    if (i < tk.len) {
-                        const int64_t p = tk.begin + i;
-                        const int q = PERM ? s.pos[p] : (int)p;
-                        s.e[q] = fmaf(-delta, Ff[s.idx[p]], s.e[q]);
-                    }
+                    for (int u = 0; u < KEEP; ++u)
+                        if (u == j) { ev = ek[u][h]; fc = fk[u][h]; }
+                } else {
+                    const int c = s.idx[p];
+                    fc = Ff[c];
+                    ev = eo[p];
+                    if (DPREV) ev = fmaf(-a.dprev[c], xp, ev);
                 }
+                eo[p] = fmaf(-delta, fc, ev);
             }
         }
     }
@@ -278,9 +287,11 @@ __global__ void __launch_bounds__(32 * kIcdMaxWarps) k_icd_split(const IcdArgs a
         if (fn >= 0) add_row(wpart, x, d, f, xf_new, fn == f ? xf_new : x[fn], lane);
         __syncwarp();
         if (lane == 0) {
+            if (a.dprev) a.xold[i] = x[a.fprev];  // before the update (fprev may be f)
             x[f] = xf_new;
             a.XT[(int64_t)f * s.n_rows + sr.row] = xf_new;
             s.delta[i] = delta;
+            a.dself[sr.row] = delta;
         }
     }
     if (fn < 0) return;
@@ -294,56 +305,72 @@ __global__ void __launch_bounds__(32 * kIcdMaxWarps) k_icd_split(const IcdArgs a
 }
 
 // Residual update of the long rows, one warp per piece of at most 128 interactions.
-template <bool PERM>
+template <bool DPREV>
 __global__ void __launch_bounds__(256) k_icd_split_resid(const IcdArgs a) {
     const StepArgs &s = a.s;
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const float *__restrict__ Ff = a.FT + (int64_t)a.f * a.n_fixed;
+    float *__restrict__ eo = a.eo;
     for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < s.n_stasks; t += nwarps) {
         const Task tk = s.stasks[t];
         const float delta = s.delta[tk.srow];
+        const float xp = DPREV ? a.xold[tk.srow] : 0.f;
         // a piece holds at most 128 interactions: four per lane, all loads issued first
-        int q[4];
-        float fc[4], ev[4];
+        float fc[4], ev[4], dp[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int i = lane + 32 * u;
-            q[u] = -1;
             if (i < tk.len) {
                 const int64_t p = tk.begin + i;
-                q[u] = PERM ? s.pos[p] : (int)p;
-                fc[u] = Ff[s.idx[p]];
+                const int c = s.idx[p];
+                fc[u] = Ff[c];
+                ev[u] = eo[p];
+                dp[u] = DPREV ? a.dprev[c] : 0.f;
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (q[u] >= 0) ev[u] = s.e[q[u]];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (q[u] >= 0) s.e[q[u]] = fmaf(-delta, fc[u], ev[u]);
+        for (int u = 0; u < 4; ++u) {
+            const int i = lane + 32 * u;
+            if (i < tk.len) {
+                const float e = DPREV ? fmaf(-dp[u], xp, ev[u]) : ev[u];
+                eo[tk.begin + i] = fmaf(-delta, fc[u], e);
+            }
+        }
     }
+}
+
+// Own-order residual copy of the item side: e_i[t] = e[pos[t]] (gather) and back (scatter).
+__global__ void k_perm_gather(const float *__restrict__ src, const int32_t *__restrict__ pos, int64_t n,
+                              float *__restrict__ dst) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = src[pos[t]];
+}
+__global__ void k_perm_scatter(const float *__restrict__ src, const int32_t *__restrict__ pos, int64_t n,
+                               float *__restrict__ dst) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        dst[pos[t]] = src[t];
 }
 
 // g and the warps' partial columns: d (1 + warps) floats, at most 4096 x 9
 constexpr int kIcdMaxSmem = (int)(sizeof(float) * 4096 * (1 + 8));
 static_assert(1024 * (1 + 32) <= 4096 * (1 + 8), "shared-memory bound of the largest d per warp count");
 
-template <bool PERM, bool HAS_A>
+template <bool HAS_A, bool DPREV>
 cudaError_t launch_icd_t(const IcdArgs &a0, cudaStream_t st) {
     IcdArgs a = a0;
     const int kIcdWarps = icd_warps(a.s.d);
     // g and the warps' partial columns; at least one float per thread for the final reduction
     const size_t smem = sizeof(float) * std::max<size_t>((size_t)a.s.d * (1 + kIcdWarps), 32 * kIcdWarps);
     prof_mark(a.s.prof, K_SPARSE, st);
-    k_icd_rows<PERM, HAS_A><<<a.grid, 32 * kIcdWarps, smem, st>>>(a);
+    k_icd_rows<HAS_A, DPREV><<<a.grid, 32 * kIcdWarps, smem, st>>>(a);
     prof_mark(a.s.prof, -1, st);
     if (a.s.n_split > 0) {
         prof_mark(a.s.prof, K_SPLIT_SOLVE, st);
         k_icd_split<<<icd_split_grid(a.s.n_split, a.s.d), 32 * kIcdWarps, smem, st>>>(a);
         prof_mark(a.s.prof, K_SPLIT_RESID, st);
         const int g3 = (int)std::min<int64_t>((a.s.n_stasks + 7) / 8, 152 * 8);
-        k_icd_split_resid<PERM><<<g3 > 0 ? g3 : 1, 256, 0, st>>>(a);
+        k_icd_split_resid<DPREV><<<g3 > 0 ? g3 : 1, 256, 0, st>>>(a);
         prof_mark(a.s.prof, -1, st);
     }
     return cudaGetLastError();
@@ -407,9 +434,21 @@ cudaError_t icd_prepare() {
 }
 
 cudaError_t launch_icd(const IcdArgs &a, cudaStream_t s) {
-    const bool perm = a.s.pos != nullptr, wa = a.s.alpha != nullptr;
-    if (perm) return wa ? launch_icd_t<true, true>(a, s) : launch_icd_t<true, false>(a, s);
-    return wa ? launch_icd_t<false, true>(a, s) : launch_icd_t<false, false>(a, s);
+    const bool dp = a.dprev != nullptr, wa = a.alpha_o != nullptr;
+    if (dp) return wa ? launch_icd_t<true, true>(a, s) : launch_icd_t<false, true>(a, s);
+    return wa ? launch_icd_t<true, false>(a, s) : launch_icd_t<false, false>(a, s);
+}
+
+cudaError_t launch_perm_gather(const float *src, const int32_t *pos, int64_t n, float *dst, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_perm_gather<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(src, pos, n, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_perm_scatter(const float *src, const int32_t *pos, int64_t n, float *dst, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_perm_scatter<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(src, pos, n, dst);
+    return cudaGetLastError();
 }
 
 }  // namespace ials
