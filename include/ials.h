@@ -227,8 +227,10 @@ ials_status ials_partial_gramian_noalloc(const float *X, int64_t n, int32_t d, i
  * set-up only.  A scheduler thread batches requests continuously: queued
  * requests are admitted in arrival order whenever their device memory fits the
  * free workspace and one of four stream slots is free, so new requests start
- * while earlier ones are still running.  A request's result does not depend on
- * the requests it is batched with. */
+ * while earlier ones are still running.  A request longer than 384
+ * interactions is split over a cluster of 8 CTAs; each request is published as
+ * soon as it finishes.  A request's result does not depend on the requests it
+ * is batched with. */
 ials_status ials_foldin_open(const float *H, int32_t n_items, const ials_params *params,
                              size_t workspace_bytes, int32_t sweeps, void *cuda_stream,
                              ials_srv **out);
@@ -254,6 +256,20 @@ ials_status ials_foldin_poll(ials_srv *srv, uint64_t ticket, float *w_out, int32
  * both taken by the library with a monotonic clock. */
 ials_status ials_foldin_poll_timed(ials_srv *srv, uint64_t ticket, float *w_out, int32_t timeout_us,
                                    double *latency_us);
+
+/* How a finished request was served (ials_foldin_poll_info). */
+typedef struct {
+    double latency_us;   /* submission to result in host memory, monotonic clock */
+    uint64_t batch;      /* id of the batch it ran in (batches are numbered from 1) */
+    int32_t batch_size;  /* requests in that batch */
+    int32_t cluster;     /* 1: longer than the library's limit for one CTA, run on a CTA cluster */
+} ials_foldin_info;
+
+/* ials_foldin_poll that also describes, in *info (if non-NULL, filled when the
+ * result is returned), how the request was served: latency, batch and whether
+ * its interactions were split over a cluster of CTAs.  Thread-safe. */
+ials_status ials_foldin_poll_info(ials_srv *srv, uint64_t ticket, float *w_out, int32_t timeout_us,
+                                  ials_foldin_info *info);
 
 /* Stop the scheduler, drop queued requests and release everything (NULL: no-op).
  * No other thread may be inside ials_foldin_submit / _poll on srv meanwhile. */

@@ -73,6 +73,10 @@ def _load():
         lib.oracle_icd.restype = C.c_int
         lib.oracle_foldin.argtypes = [vp, i32, i32, i32, f64, f64, f64, i32, vp, vp, vp, i32, vp]
         lib.oracle_foldin.restype = C.c_int
+        lib.oracle_foldin_g.argtypes = [vp, vp, i32, i32, i32, f64, f64, f64, i32, vp, vp, vp, i32, vp]
+        lib.oracle_foldin_g.restype = C.c_int
+        lib.oracle_gramian.argtypes = [vp, i32, i32, vp]
+        lib.oracle_gramian.restype = None
         _lib = lib
     return _lib
 
@@ -206,14 +210,29 @@ def icd(P: Problem, epochs: int, W, H):
     return W, H, yhat, st
 
 
-def foldin(H, d, b, alpha0, lam, nu, sweeps, items, y=None, alpha=None):
-    """Embedding of a new user against frozen H; returns (w, status)."""
+def gramian(H):
+    """G^I = H^T H (Eq. 4) in FP64, for repeated fold-ins against the same H."""
+    H = _c(H, np.float64)
+    G = np.empty((H.shape[1], H.shape[1]))
+    _load().oracle_gramian(_ptr(H), H.shape[0], H.shape[1], _ptr(G))
+    return G
+
+
+def foldin(H, d, b, alpha0, lam, nu, sweeps, items, y=None, alpha=None, G=None):
+    """Embedding of a new user against frozen H; returns (w, status).  With G (from
+    gramian(H)) the Gramian is not formed again."""
     H = _c(H, np.float64)
     assert H.ndim == 2 and H.shape[1] == d
     items = _c(items, np.int32)
     y = None if y is None else _c(y, np.float64)
     alpha = None if alpha is None else _c(alpha, np.float64)
     w = np.empty(d)
-    st = _load().oracle_foldin(_ptr(H), H.shape[0], d, b, alpha0, lam, nu, sweeps, _ptr(items),
-                               _ptr(y), _ptr(alpha), items.size, _ptr(w))
+    if G is None:
+        st = _load().oracle_foldin(_ptr(H), H.shape[0], d, b, alpha0, lam, nu, sweeps, _ptr(items),
+                                   _ptr(y), _ptr(alpha), items.size, _ptr(w))
+    else:
+        G = _c(G, np.float64)
+        assert G.shape == (d, d)
+        st = _load().oracle_foldin_g(_ptr(H), _ptr(G), H.shape[0], d, b, alpha0, lam, nu, sweeps,
+                                     _ptr(items), _ptr(y), _ptr(alpha), items.size, _ptr(w))
     return w, st

@@ -20,7 +20,8 @@
  *   oracle_icd             T epochs of Algorithm 2 (Eqs. 5-7)
  *   oracle_foldin          new-user solve against frozen H (Section 5.1.1
  *                          protocol; the paper does not give the procedure,
- *                          see the reading in oracle_foldin)
+ *                          see the reading in oracle_foldin); oracle_foldin_g
+ *                          takes G^I from oracle_gramian instead of forming it
  *
  * Readings of the paper that this file fixes:
  *  - The 1/2 in front of the gradient and Hessian cancels in the Newton step
@@ -554,18 +555,38 @@ int oracle_icd(const oracle_problem *P, int epochs, double *W, double *H, double
  * and hence G^I, fixed and lambda_u = lambda (1 + nu n).  One sweep with b = d
  * is Eq. 3; more sweeps converge to it for any b.
  * items/y/alpha: the request's n interactions (y, alpha may be NULL = 1). */
+/* G^I = H^T H (Eq. 4), d x d, for callers that fold in many users against the
+ * same frozen H (oracle_foldin_g). */
+void oracle_gramian(const double *H, int32_t n_items, int32_t d, double *G) { gramian(H, n_items, d, G); }
+
+/* oracle_foldin with G^I = H^T H given (from oracle_gramian), so that a
+ * sequence of requests against one H forms it once.  Same arithmetic. */
+int oracle_foldin_g(const double *H, const double *G, int32_t n_items, int32_t d, int32_t b, double alpha0,
+                    double lambda, double nu, int32_t sweeps, const int32_t *items, const double *y,
+                    const double *alpha, int32_t n, double *w_out);
+
 int oracle_foldin(const double *H, int32_t n_items, int32_t d, int32_t b, double alpha0,
                   double lambda, double nu, int32_t sweeps, const int32_t *items,
                   const double *y, const double *alpha, int32_t n, double *w_out) {
     if (d <= 0 || b <= 0 || n < 0) return ORACLE_EINVAL;
+    double *G = malloc(sizeof(double) * d * d);
+    if (!G) return ORACLE_ENOMEM;
+    gramian(H, n_items, d, G); /* G^I, Eq. 4 */
+    const int st = oracle_foldin_g(H, G, n_items, d, b, alpha0, lambda, nu, sweeps, items, y, alpha, n, w_out);
+    free(G);
+    return st;
+}
+
+int oracle_foldin_g(const double *H, const double *G, int32_t n_items, int32_t d, int32_t b, double alpha0,
+                    double lambda, double nu, int32_t sweeps, const int32_t *items, const double *y,
+                    const double *alpha, int32_t n, double *w_out) {
+    if (d <= 0 || b <= 0 || n < 0) return ORACLE_EINVAL;
     for (int32_t s = 0; s < n; ++s)
         if (items[s] < 0 || items[s] >= n_items) return ORACLE_EINVAL;
     const int bmax = b < d ? b : d;
-    double *G = malloc(sizeof(double) * d * d);
     double *yhat = malloc(sizeof(double) * (n > 0 ? n : 1));
     double *A = malloc(sizeof(double) * (bmax * bmax + bmax));
-    if (!G || !yhat || !A) { free(G); free(yhat); free(A); return ORACLE_ENOMEM; }
-    gramian(H, n_items, d, G); /* G^I, Eq. 4 */
+    if (!yhat || !A) { free(yhat); free(A); return ORACLE_ENOMEM; }
     double *g = A + bmax * bmax;
     const double lam = lambda * (1.0 + nu * (double)n);
     int status = ORACLE_OK;
@@ -600,7 +621,6 @@ int oracle_foldin(const double *H, int32_t n_items, int32_t d, int32_t b, double
             }
         }
     }
-    free(G);
     free(yhat);
     free(A);
     return status;

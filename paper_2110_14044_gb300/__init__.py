@@ -123,6 +123,14 @@ class FoldinServer:
             raise IalsError(st, ials_last_error())
         return w
 
+    def result_info(self, ticket, timeout_s=60.0):
+        """(embedding, info): info gives latency_us, batch, batch_size and cluster."""
+        w = np.empty(self.d, np.float32)
+        st, info = _abi.ials_foldin_poll_info(self.srv, ticket, w, int(timeout_s * 1e6))
+        if st != _abi.OK:
+            raise IalsError(st, ials_last_error())
+        return w, info
+
     def close(self):
         if getattr(self, "srv", None) is not None:
             ials_foldin_close(self.srv)

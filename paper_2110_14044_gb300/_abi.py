@@ -30,7 +30,7 @@ EXPORTS = (
     "ials_last_stats", "ials_partial_gramian", "ials_last_error", "ials_profile_epochs",
     "ials_work_model", "ials_partial_gramian_noalloc", "ials_partial_gramian_bf16",
     "ials_foldin_open", "ials_foldin_submit", "ials_foldin_poll", "ials_foldin_close",
-    "ials_foldin_poll_timed",
+    "ials_foldin_poll_timed", "ials_foldin_poll_info",
 )
 
 KERNEL_KINDS = ("residual", "gram", "rowterm", "sparse", "split_solve", "split_resid", "retry",
@@ -41,6 +41,11 @@ class IalsError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+class ials_foldin_info(C.Structure):
+    _fields_ = [("latency_us", C.c_double), ("batch", C.c_uint64), ("batch_size", C.c_int32),
+                ("cluster", C.c_int32)]
 
 
 class ials_params(C.Structure):
@@ -84,6 +89,7 @@ def lib():
             "ials_foldin_poll": ([vp, C.c_uint64, vp, i32], st),
             "ials_foldin_close": ([vp], st),
             "ials_foldin_poll_timed": ([vp, C.c_uint64, vp, i32, C.POINTER(C.c_double)], st),
+            "ials_foldin_poll_info": ([vp, C.c_uint64, vp, i32, C.POINTER(ials_foldin_info)], st),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -259,3 +265,17 @@ def ials_foldin_poll_timed(srv, ticket, w_out, timeout_us=0):
     if status not in (OK, EAGAIN, ETIMEDOUT, ENOTPD):
         _check(status)
     return status, (lat.value if status in (OK, ENOTPD) else None)
+
+
+def ials_foldin_poll_info(srv, ticket, w_out, timeout_us=0):
+    """(status, info dict or None): how a finished request was served (latency, batch,
+    batch size, whether it ran on a CTA cluster)."""
+    info = ials_foldin_info()
+    status = lib().ials_foldin_poll_info(srv, C.c_uint64(ticket), _ptr(w_out), int(timeout_us),
+                                         C.byref(info))
+    if status not in (OK, EAGAIN, ETIMEDOUT, ENOTPD):
+        _check(status)
+    if status not in (OK, ENOTPD):
+        return status, None
+    return status, {"latency_us": info.latency_us, "batch": info.batch, "batch_size": info.batch_size,
+                    "cluster": bool(info.cluster)}

@@ -5,17 +5,22 @@
 // scheduler thread owns the device side.  It admits queued requests in arrival
 // order into a batch as long as the batch's device memory fits the free part of
 // a fixed workspace arena (memory admission), uploads the batch's inputs with
-// one copy, launches the fold-in kernel (one CTA per request) on one of
-// several streams and downloads the embeddings with one copy.  Up to
-// kSlots batches are in flight at once, so requests that arrive while others
-// run are admitted as soon as a stream slot and memory free up and their work
-// overlaps on the device.  Finished batches release their memory and wake
-// poll() callers.  Each request runs on its own CTA in a fixed order, so its
-// result does not depend on the batch it lands in.
+// one copy and launches two fold-in kernels on one of several stream pairs:
+// short requests on one CTA each, long ones (more than kFoldLong interactions)
+// on a cluster of kFoldCluster CTAs each, so a long history no longer sets the
+// latency of everything batched with it.  Up to kSlots batches are in flight at
+// once, so requests that arrive while others run are admitted as soon as a
+// stream slot and memory free up and their work overlaps on the device.  Every
+// request writes its embedding and a completion flag to mapped host memory as
+// it finishes; the scheduler publishes it at once (waking poll() callers) and
+// returns the batch's memory when the whole batch is done.  Which kernel a
+// request takes depends on its length alone, so its result does not depend on
+// the batch it lands in.
 #include "ials_internal.cuh"
 #include "../../include/ials.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -57,6 +62,9 @@ struct Request {
     bool done = false;
     int status = 0;
     std::vector<float> w;
+    uint64_t batch = 0;   // batch it ran in
+    int batch_size = 0;   // requests in that batch
+    bool cluster = false;  // ran on a CTA cluster
 };
 
 // First-fit allocator over [0, size) with coalescing frees.
@@ -97,18 +105,20 @@ struct Arena {
 };
 
 struct Slot {
-    cudaStream_t stream = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaStream_t stream = nullptr, stream2 = nullptr;  // short requests; long requests
+    cudaEvent_t ev = nullptr, ev_in = nullptr, ev2 = nullptr;
     bool busy = false;
     std::vector<std::shared_ptr<Request>> reqs;
     size_t off = 0, bytes = 0, out_off = 0;
     // pinned host staging (grown on demand) and device request table
     void *h_in = nullptr;
     size_t h_in_cap = 0;
-    float *h_out = nullptr;
-    size_t h_out_cap = 0;
     FoldReq *h_req = nullptr, *d_req = nullptr;
-    int32_t *h_st = nullptr, *d_st = nullptr;
+    int32_t *h_list = nullptr, *d_list = nullptr;
+    int32_t *d_st = nullptr;
+    // mapped host memory the kernels write: embeddings (kMaxBatch x d), flags
+    float *h_out = nullptr, *m_out = nullptr;
+    int32_t *h_done = nullptr, *m_done = nullptr;
 };
 
 }  // namespace
@@ -126,7 +136,7 @@ struct ials_srv {
     std::condition_variable cv_sched, cv_done;
     std::deque<std::shared_ptr<Request>> pending;
     std::unordered_map<uint64_t, std::shared_ptr<Request>> table;
-    uint64_t next_ticket = 1;
+    uint64_t next_ticket = 1, next_batch = 1;
     bool stop = false;
     std::string error;
     std::thread worker;
@@ -136,15 +146,36 @@ struct ials_srv {
                align_up(4 * (size_t)foldin_factor_floats(d, b)) + align_up(4 * (size_t)d);
     }
 
-    void retire(Slot &s) {
+    // Publish the requests of slot s whose completion flag the kernels have set.
+    bool publish(Slot &s) {
+        bool any = false;
         const auto now = std::chrono::steady_clock::now();
         for (size_t i = 0; i < s.reqs.size(); ++i) {
-            s.reqs[i]->t_done = now;
             Request &r = *s.reqs[i];
+            if (r.done) continue;
+            const int32_t f = reinterpret_cast<volatile int32_t *>(s.h_done)[i];
+            if (f == 0) continue;
+            std::atomic_thread_fence(std::memory_order_acquire);
             r.w.assign(s.h_out + i * d, s.h_out + (i + 1) * d);
-            r.status = s.h_st[i];
+            r.status = f - 1;
+            r.t_done = now;
             r.done = true;
+            any = true;
         }
+        return any;
+    }
+
+    // The whole batch is done: every request is published; the memory returns.
+    void retire(Slot &s) {
+        publish(s);
+        const auto now = std::chrono::steady_clock::now();
+        for (auto &r : s.reqs)
+            if (!r->done) {  // a finished batch without the request's flag: report it as failed
+                r->t_done = now;
+                r->status = IALS_ECUDA;
+                r->done = true;
+                error = "fold-in request finished without its completion flag";
+            }
         alloc.release(s.off, s.bytes);
         s.reqs.clear();
         s.busy = false;
@@ -156,6 +187,7 @@ struct ials_srv {
         error = std::string("fold-in batch: ") + cudaGetErrorString(err);
         const auto now = std::chrono::steady_clock::now();
         for (auto &r : s.reqs) {
+            if (r->done) continue;
             r->t_done = now;
             r->status = IALS_ECUDA;
             r->done = true;
@@ -183,7 +215,8 @@ struct ials_srv {
         if (k == 0) return false;
         size_t off;
         if (!alloc.alloc(total, off)) return false;
-        // layout: [inputs of all requests | outputs (k x d) | e and factors]
+        // layout: [inputs of all requests | outputs (k x d, unused: results go to mapped
+        // host memory) | e and factors]
         std::vector<size_t> in_off(k), sc_off(k);
         size_t cur = 0;
         for (int i = 0; i < k; ++i) {
@@ -213,20 +246,19 @@ struct ials_srv {
                 return false;
             }
         }
-        if ((size_t)k * d > s.h_out_cap) {
-            if (s.h_out) cudaFreeHost(s.h_out);
-            s.h_out_cap = std::max((size_t)k * d, 2 * s.h_out_cap);
-            if (cudaHostAlloc((void **)&s.h_out, s.h_out_cap * 4, cudaHostAllocDefault) != cudaSuccess) {
-                cudaGetLastError();
-                s.h_out = nullptr;
-                s.h_out_cap = 0;
-                alloc.release(off, total);
-                error = "pinned staging allocation failed";
-                return false;
-            }
-        }
         s.reqs.assign(pending.begin(), pending.begin() + k);
         pending.erase(pending.begin(), pending.begin() + k);
+        const uint64_t batch = next_batch++;
+        int n_short = 0;
+        for (int i = 0; i < k; ++i) {
+            s.reqs[i]->batch = batch;
+            s.reqs[i]->batch_size = k;
+            s.reqs[i]->cluster = (int)s.reqs[i]->items.size() > kFoldLong;
+            if (!s.reqs[i]->cluster) s.h_list[n_short++] = i;
+        }
+        for (int i = 0, j = n_short; i < k; ++i)  // short requests first, then long ones
+            if (s.reqs[i]->cluster) s.h_list[j++] = i;
+        std::memset(s.h_done, 0, sizeof(int32_t) * k);
         uint8_t *hin = static_cast<uint8_t *>(s.h_in);
         for (int i = 0; i < k; ++i) {
             const Request &r = *s.reqs[i];
@@ -246,6 +278,10 @@ struct ials_srv {
         FoldArgs a;
         a.req = s.d_req;
         a.n_req = k;
+        a.list = s.d_list;
+        a.n_list = n_short;
+        a.w_host = s.m_out;
+        a.done_host = s.m_done;
         a.arena = arena;
         a.H = H;
         a.G = G;
@@ -259,17 +295,26 @@ struct ials_srv {
         cudaError_t e = cudaMemcpyAsync(arena + off, hin, in_bytes, cudaMemcpyHostToDevice, s.stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(s.d_req, s.h_req, sizeof(FoldReq) * k, cudaMemcpyHostToDevice, s.stream);
-        if (e == cudaSuccess) e = launch_foldin(a, s.stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s.h_out, arena + off + out_off, 4 * (size_t)d * k, cudaMemcpyDeviceToHost,
-                                s.stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s.h_st, s.d_st, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, s.stream);
+            e = cudaMemcpyAsync(s.d_list, s.h_list, sizeof(int32_t) * k, cudaMemcpyHostToDevice, s.stream);
+        const bool any_long = n_short < k;
+        if (e == cudaSuccess && any_long) e = cudaEventRecord(s.ev_in, s.stream);
+        if (e == cudaSuccess && any_long) e = cudaStreamWaitEvent(s.stream2, s.ev_in, 0);
+        if (e == cudaSuccess && any_long) {  // long requests: one CTA cluster each, on the second stream
+            FoldArgs al = a;
+            al.list = s.d_list + n_short;
+            al.n_list = k - n_short;
+            e = launch_foldin(al, true, s.stream2);
+        }
+        if (e == cudaSuccess) e = launch_foldin(a, false, s.stream);
+        if (e == cudaSuccess && any_long) e = cudaEventRecord(s.ev2, s.stream2);
+        if (e == cudaSuccess && any_long) e = cudaStreamWaitEvent(s.stream, s.ev2, 0);
         if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.stream);
         if (e != cudaSuccess) {
             error = std::string("fold-in launch: ") + cudaGetErrorString(e);
             cudaGetLastError();
             cudaStreamSynchronize(s.stream);
+            cudaStreamSynchronize(s.stream2);
             const auto now = std::chrono::steady_clock::now();
             for (auto &r : s.reqs) {
                 r->t_done = now;
@@ -301,6 +346,8 @@ struct ials_srv {
                 } else if (q != cudaErrorNotReady) {
                     fail_slot(s, q);
                     progressed = true;
+                } else if (publish(s)) {
+                    cv_done.notify_all();  // requests finished ahead of their batch
                 }
             }
             cudaGetLastError();  // a not-ready query is not an error
@@ -320,8 +367,10 @@ struct ials_srv {
             }
         }
         lk.unlock();
-        for (Slot &s : slots)
+        for (Slot &s : slots) {
             if (s.stream) cudaStreamSynchronize(s.stream);
+            if (s.stream2) cudaStreamSynchronize(s.stream2);
+        }
     }
 
     ~ials_srv() {
@@ -333,12 +382,17 @@ struct ials_srv {
         if (worker.joinable()) worker.join();
         for (Slot &s : slots) {
             if (s.ev) cudaEventDestroy(s.ev);
+            if (s.ev_in) cudaEventDestroy(s.ev_in);
+            if (s.ev2) cudaEventDestroy(s.ev2);
             if (s.stream) cudaStreamDestroy(s.stream);
+            if (s.stream2) cudaStreamDestroy(s.stream2);
             if (s.h_in) cudaFreeHost(s.h_in);
             if (s.h_out) cudaFreeHost(s.h_out);
+            if (s.h_done) cudaFreeHost(s.h_done);
             if (s.h_req) cudaFreeHost(s.h_req);
-            if (s.h_st) cudaFreeHost(s.h_st);
+            if (s.h_list) cudaFreeHost(s.h_list);
             if (s.d_req) cudaFree(s.d_req);
+            if (s.d_list) cudaFree(s.d_list);
             if (s.d_st) cudaFree(s.d_st);
         }
         if (H) cudaFree(H);
@@ -392,10 +446,18 @@ ials_status ials_foldin_open(const float *H, int32_t n_items, const ials_params 
     }
     for (Slot &sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&sl.stream2, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.ev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.ev2, cudaEventDisableTiming) != cudaSuccess ||
             cudaHostAlloc((void **)&sl.h_req, sizeof(FoldReq) * kMaxBatch, cudaHostAllocDefault) != cudaSuccess ||
-            cudaHostAlloc((void **)&sl.h_st, sizeof(int32_t) * kMaxBatch, cudaHostAllocDefault) != cudaSuccess ||
+            cudaHostAlloc((void **)&sl.h_list, sizeof(int32_t) * kMaxBatch, cudaHostAllocDefault) != cudaSuccess ||
+            cudaHostAlloc((void **)&sl.h_out, sizeof(float) * (size_t)kMaxBatch * p.d, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostAlloc((void **)&sl.h_done, sizeof(int32_t) * kMaxBatch, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer((void **)&sl.m_out, sl.h_out, 0) != cudaSuccess ||
+            cudaHostGetDevicePointer((void **)&sl.m_done, sl.h_done, 0) != cudaSuccess ||
             cudaMalloc(&sl.d_req, sizeof(FoldReq) * kMaxBatch) != cudaSuccess ||
+            cudaMalloc(&sl.d_list, sizeof(int32_t) * kMaxBatch) != cudaSuccess ||
             cudaMalloc(&sl.d_st, sizeof(int32_t) * kMaxBatch) != cudaSuccess) {
             cudaGetLastError();
             return sfail(IALS_ENOMEM, "fold-in streams or staging");
@@ -438,8 +500,19 @@ ials_status ials_foldin_submit(ials_srv *s, const int32_t *items, const float *y
     return IALS_OK;
 }
 
+ials_status ials_foldin_poll_info(ials_srv *s, uint64_t ticket, float *w_out, int32_t timeout_us,
+                                  ials_foldin_info *info);
+
 ials_status ials_foldin_poll_timed(ials_srv *s, uint64_t ticket, float *w_out, int32_t timeout_us,
                                    double *latency_us) {
+    ials_foldin_info info;
+    const ials_status st = ials_foldin_poll_info(s, ticket, w_out, timeout_us, &info);
+    if (latency_us && (st == IALS_OK || st == IALS_ENOTPD)) *latency_us = info.latency_us;
+    return st;
+}
+
+ials_status ials_foldin_poll_info(ials_srv *s, uint64_t ticket, float *w_out, int32_t timeout_us,
+                                  ials_foldin_info *info) {
     if (!s || !w_out) return sfail(IALS_EINVAL, "bad poll arguments");
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->table.find(ticket);
@@ -449,8 +522,12 @@ ials_status ials_foldin_poll_timed(ials_srv *s, uint64_t ticket, float *w_out, i
         s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return r->done; });
     if (!r->done) return timeout_us > 0 ? sfail(IALS_ETIMEDOUT, "result not ready") : IALS_EAGAIN;
     std::memcpy(w_out, r->w.data(), sizeof(float) * (size_t)s->d);
-    if (latency_us)
-        *latency_us = std::chrono::duration<double, std::micro>(r->t_done - r->t_submit).count();
+    if (info) {
+        info->latency_us = std::chrono::duration<double, std::micro>(r->t_done - r->t_submit).count();
+        info->batch = r->batch;
+        info->batch_size = r->batch_size;
+        info->cluster = r->cluster ? 1 : 0;
+    }
     const int st = r->status;
     s->table.erase(it);
     if (st == 4) return sfail(IALS_ENOTPD, "a block Hessian was not positive definite");

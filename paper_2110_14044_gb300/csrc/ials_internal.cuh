@@ -161,13 +161,20 @@ struct FoldReq {
 struct FoldArgs {
     const FoldReq *req;
     int32_t n_req;
+    const int32_t *list;  // the requests this launch serves (indices into req)
+    int32_t n_list;
     uint8_t *arena;
     const float *H;   // frozen item factors, n_items x d
     const float *G;   // G^I = H^T H, d x d
     int32_t d, b, sweeps;
     float alpha0, lambda, nu;
-    int32_t *status;  // per request: 0 ok, 4 not positive definite
+    int32_t *status;     // per request: 0 ok, 4 not positive definite
+    float *w_host;       // mapped host memory: the embeddings, n_req x d
+    int32_t *done_host;  // mapped host memory: per request 1 + status once finished
 };
+// Requests longer than kFoldLong interactions run on a cluster of kFoldCluster CTAs.
+constexpr int kFoldLong = 384;
+constexpr int kFoldCluster = 8;
 
 // ---------------------------------------------------------------- launchers
 // dense kernels (k_dense.cu)
@@ -256,8 +263,9 @@ cudaError_t launch_sparse_b32(const StepArgs &a, cudaStream_t s);
 // block sizes 64 and 128 (k_sparse_b64.cu, k_sparse_b128.cu): one CTA per task
 cudaError_t launch_sparse_b64(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_sparse_b128(const StepArgs &a, cudaStream_t s);
-// fold-in (k_foldin.cu): one CTA per request; factors per request: foldin_factor_floats
-cudaError_t launch_foldin(const FoldArgs &a, cudaStream_t s);
+// fold-in (k_foldin.cu): one CTA per request, or (cluster) one cluster of
+// kFoldCluster CTAs per request; factors per request: foldin_factor_floats
+cudaError_t launch_foldin(const FoldArgs &a, bool cluster, cudaStream_t s);
 int64_t foldin_factor_floats(int32_t d, int32_t b);
 // BF16 mode (k_sparse_bf16.cu): tensor-core statistics for block sizes 16 and 32
 cudaError_t launch_sparse_bf16_b16(const StepArgs &a, cudaStream_t s);

@@ -80,20 +80,50 @@ def test_foldin_result_does_not_depend_on_the_batch():
     probe = rng.choice(2000, 500, replace=False).astype(np.int32)
     alone = srv.result(srv.submit(probe))
     others = requests(2000, 400, 3, max_len=2000)
-    results = {}
 
     def flood(part):
         for it, y in part:
             srv.submit(it, y)
 
-    threads = [threading.Thread(target=flood, args=(others[k::4],)) for k in range(4)]
-    for t in threads:
-        t.start()
-    mixed_ticket = srv.submit(probe)
-    for t in threads:
-        t.join()
-    mixed = srv.result(mixed_ticket)
-    np.testing.assert_array_equal(alone, mixed)
+    shared = False
+    for attempt in range(5):  # until the probe is seen to share its batch with others
+        threads = [threading.Thread(target=flood, args=(others[k::4],)) for k in range(4)]
+        for t in threads:
+            t.start()
+        mixed_ticket = srv.submit(probe)
+        for t in threads:
+            t.join()
+        mixed, info = srv.result_info(mixed_ticket)
+        np.testing.assert_array_equal(alone, mixed)
+        assert info["cluster"]  # 500 interactions: split over a CTA cluster
+        if info["batch_size"] > 1:
+            shared = True
+            break
+    assert shared, "the probe never landed in a batch with other requests"
+    srv.close()
+
+
+@pytest.mark.parametrize("n", [1, 384, 385, 3000])
+def test_foldin_long_requests_on_clusters_match_oracle(n):
+    """Requests above the one-CTA limit run on a cluster of CTAs that share the
+    interactions; the result still matches the oracle, and a short request in the
+    same batch is unaffected."""
+    rng = np.random.default_rng(10 + n)
+    d, b, n_items = 256, 64, 5000
+    H = rng.normal(0, 0.05, (n_items, d)).astype(np.float32)
+    srv = server(H, d, b, 0.1, 1e-3, 1.0, sweeps=4, workspace_bytes=1 << 30)
+    items = rng.choice(n_items, n, replace=False).astype(np.int32)
+    y = rng.uniform(0.5, 2.0, n).astype(np.float32)
+    short = rng.choice(n_items, 50, replace=False).astype(np.int32)
+    t1, t2 = srv.submit(items, y), srv.submit(short)
+    w, info = srv.result_info(t1)
+    w2, info2 = srv.result_info(t2)
+    assert info["cluster"] == (n > 384) and not info2["cluster"]
+    ref, st = oracle.foldin(H, d, b, 0.1, 1e-3, 1.0, 4, items, y=y)
+    assert st == 0
+    assert rel(w, ref) <= TOL, rel(w, ref)
+    ref2, _ = oracle.foldin(H, d, b, 0.1, 1e-3, 1.0, 4, short)
+    assert rel(w2, ref2) <= TOL
     srv.close()
 
 

@@ -387,3 +387,18 @@ def test_epochs_reach_a_stationary_point_of_the_loss(b):
                  H1.ravel().copy(), range(H1.size))
     assert max(np.abs(gW).max(), np.abs(gH).max()) < 1e-8
     assert abs(trace[-1] - brute_loss(data, y, alpha, W1, H1, a0, lam, nu)) < 1e-10 * trace[-1]
+
+
+def test_foldin_with_precomputed_gramian_is_the_same_computation():
+    """oracle.foldin with G^I from oracle.gramian (formed once for many requests)
+    gives bitwise the result of forming it inside the call, and G^I is H^T H."""
+    rng = np.random.default_rng(77)
+    H = rng.normal(0, 0.1, (60, 12))
+    G = oracle.gramian(H)
+    np.testing.assert_allclose(G, H.T @ H, rtol=1e-12, atol=1e-14)
+    items = rng.choice(60, 17, replace=False).astype(np.int32)
+    y = rng.uniform(0.5, 2.0, 17)
+    w1, s1 = oracle.foldin(H, 12, 4, 0.1, 1e-2, 0.5, 3, items, y=y)
+    w2, s2 = oracle.foldin(H, 12, 4, 0.1, 1e-2, 0.5, 3, items, y=y, G=G)
+    assert s1 == s2 == 0
+    assert np.array_equal(w1, w2)
