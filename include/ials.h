@@ -60,9 +60,9 @@ enum {
     IALS_PREC_FP32 = 0,  /* FP32 everywhere (FP64 objective, FP64 retry of failed pivots) */
     IALS_PREC_BF16 = 1   /* BF16 tensor-core statistics: x = hi + lo split into two bf16,
                           * products hi*hi + hi*lo + lo*hi accumulated in FP32 (about 16
-                          * bits); FP32 solve with FP64 retry, FP64 objective.  Needs
-                          * b in {16, 32, 64, 128}, d % 8 == 0 and unweighted data
-                          * (alpha NULL). */
+                          * bits); weighted interactions enter as rows scaled by
+                          * sqrt(alpha); FP32 solve with FP64 retry, FP64 objective.
+                          * Needs b in {16, 32, 64, 128} and d % 8 == 0. */
 };
 
 /* ials_params.flags */

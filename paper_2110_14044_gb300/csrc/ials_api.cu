@@ -520,9 +520,8 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
         return fail(IALS_EINVAL, "alpha0, lambda, nu must be finite and >= 0");
     if (p.precision != IALS_PREC_FP32 && p.precision != IALS_PREC_BF16)
         return fail(IALS_EINVAL, "unknown precision");
-    if (p.precision == IALS_PREC_BF16 &&
-        ((p.b != 16 && p.b != 32 && p.b != 64 && p.b != 128) || p.d % 8 != 0 || alpha))
-        return fail(IALS_EINVAL, "BF16 precision needs b in {16, 32, 64, 128}, d % 8 == 0 and unweighted data");
+    if (p.precision == IALS_PREC_BF16 && ((p.b != 16 && p.b != 32 && p.b != 64 && p.b != 128) || p.d % 8 != 0))
+        return fail(IALS_EINVAL, "BF16 precision needs b in {16, 32, 64, 128} and d % 8 == 0");
     if (n_users <= 0 || n_items <= 0) return fail(IALS_EINVAL, "n_users and n_items must be > 0");
     if (nnz < 0 || nnz >= (int64_t)1 << 31) return fail(IALS_EINVAL, "nnz must be in [0, 2^31)");
     if (!u_indptr || (nnz > 0 && !u_items)) return fail(IALS_EINVAL, "user CSR missing");

@@ -19,6 +19,10 @@
 // residual update e_s -= <delta, f_s> is again a tensor-core product: the
 // staged tile times delta (split hi + lo, compensated the same way) as the
 // only non-zero column of an m16n8k16 B operand.
+// Weighted data: sum_s alpha_s f f^T = X~^T X~ with the rows of X~ = sqrt(alpha_s)
+// f_s, and sum_s alpha_s e_s f_s = X~^T (sqrt(alpha) e), so each staged row and its
+// residual are scaled by sqrt(alpha_s) (and split into hi / lo again) before the
+// products; the residual update uses the slices unscaled, gathered again.
 #pragma once
 
 #include "k_sparse_impl.cuh"
@@ -34,7 +38,7 @@ struct BfCfg {
     static constexpr int TILE = CH * SBH;       // bf16 elements of one hi (or lo) tile
     static constexpr int BUF_BYTES = 2 * TILE * 2;
     static constexpr int SA = B + 4;            // float row stride of the shared A_r (in buffer 1)
-    static constexpr int WARP_BYTES = 2 * BUF_BYTES + B * 4 + 16;
+    static constexpr int WARP_BYTES = 2 * BUF_BYTES + B * 4 + 16 + 2 * CH * 4;  // + sqrt(alpha) per staged row
     static constexpr int WARPS = 8;
     static constexpr int SMEM_BYTES = B * B * 4 + WARPS * WARP_BYTES;
     static_assert(B * SA * 4 <= BUF_BYTES, "A_r must fit a staging buffer");
@@ -122,6 +126,34 @@ __device__ __forceinline__ float project_mma(const __nv_bfloat16 *th, const __nv
     return out;
 }
 
+// Weighted data: row k (< cnt) of the staged hi / lo tiles becomes the hi / lo
+// split of sqrt(alpha_k) (hi + lo); lane k takes row k.
+template <int B>
+__device__ __forceinline__ void scale_rows(__nv_bfloat16 *th, __nv_bfloat16 *tl, const float *sal, int cnt,
+                                           int lane) {
+    constexpr int SBH = BfCfg<B>::SBH;
+    if (lane >= cnt) return;
+    const float sa = sal[lane];
+#pragma unroll
+    for (int v = 0; v < B / 8; ++v) {
+        uint4 hv = reinterpret_cast<uint4 *>(th + lane * SBH)[v];
+        uint4 lv = reinterpret_cast<uint4 *>(tl + lane * SBH)[v];
+        __nv_bfloat162 *h2 = reinterpret_cast<__nv_bfloat162 *>(&hv);
+        __nv_bfloat162 *l2 = reinterpret_cast<__nv_bfloat162 *>(&lv);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 hf = __bfloat1622float2(h2[q]), lf = __bfloat1622float2(l2[q]);
+            const float x0 = (hf.x + lf.x) * sa, x1 = (hf.y + lf.y) * sa;
+            const __nv_bfloat162 nh = __floats2bfloat162_rn(x0, x1);
+            const float2 nhf = __bfloat1622float2(nh);
+            h2[q] = nh;
+            l2[q] = __floats2bfloat162_rn(x0 - nhf.x, x1 - nhf.y);
+        }
+        reinterpret_cast<uint4 *>(th + lane * SBH)[v] = hv;
+        reinterpret_cast<uint4 *>(tl + lane * SBH)[v] = lv;
+    }
+}
+
 // Gather the hi and lo slices of `cnt` interactions (column id of interaction k in lane k).
 template <int B>
 __device__ __forceinline__ void gather_hilo(__nv_bfloat16 *th, __nv_bfloat16 *tl,
@@ -144,7 +176,7 @@ __device__ __forceinline__ void gather_hilo(__nv_bfloat16 *th, __nv_bfloat16 *tl
     }
 }
 
-template <int B, bool PERM>
+template <int B, bool PERM, bool HAS_A>
 __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
     using C = BfCfg<B>;
     constexpr int SBH = C::SBH, CH = C::CH, MT = C::MT, SA = C::SA;
@@ -159,6 +191,7 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
     // staging buffer bi: hi tile at wb + bi * BUF_BYTES, lo tile right after it
     auto th_of = [&](int bi) { return reinterpret_cast<__nv_bfloat16 *>(wb + bi * C::BUF_BYTES); };
     float *vv = reinterpret_cast<float *>(wb + 2 * C::BUF_BYTES);
+    float *sal = vv + B + 4;  // sqrt(alpha) of the rows staged in buffer bi: sal[bi * CH + k]
     for (int i = lane; i < 2 * C::BUF_BYTES / 16; i += 32)
         reinterpret_cast<uint4 *>(wb)[i] = make_uint4(0u, 0u, 0u, 0u);  // padding columns stay zero
     __syncthreads();
@@ -185,7 +218,7 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
             for (int q = 0; q < 4; ++q) gac[t][q] = 0.f;
         int cB = 0;
         int64_t qB = 0;
-        float eB = 0.f;
+        float eB = 0.f, aB = 1.f;
         auto load_meta = [&](int j) {
             const int cnt = min(CH, tk.len - j * CH);
             if (lane < cnt) {
@@ -193,15 +226,22 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
                 cB = a.idx[s];
                 qB = PERM ? (int64_t)a.pos[s] : s;
                 eB = a.e[qB];
+                if (HAS_A) aB = a.alpha[qB];
             }
         };
         auto issue = [&](int j, int bi) {
             const int cnt = min(CH, tk.len - j * CH);
             __nv_bfloat16 *th = th_of(bi), *tl = th + C::TILE;
-            if (lane < cnt) {  // residual column
-                const __nv_bfloat16 h = __float2bfloat16_rn(eB);
+            if (lane < cnt) {  // residual column (times sqrt(alpha) for weighted data)
+                float ew = eB;
+                if (HAS_A) {
+                    const float sa = sqrtf(aB);
+                    sal[bi * CH + lane] = sa;
+                    ew *= sa;
+                }
+                const __nv_bfloat16 h = __float2bfloat16_rn(ew);
                 th[lane * SBH + B] = h;
-                tl[lane * SBH + B] = __float2bfloat16_rn(eB - __bfloat162float(h));
+                tl[lane * SBH + B] = __float2bfloat16_rn(ew - __bfloat162float(h));
             } else if (lane < ((cnt + 15) & ~15)) {  // rows past the end of a short chunk: zero
 #pragma unroll
                 for (int v = 0; v < SBH / 8; ++v) {
@@ -229,6 +269,10 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
             }
             const int cnt = min(CH, tk.len - ch * CH);
             const __nv_bfloat16 *th = th_of(bi), *tl = th + C::TILE;
+            if (HAS_A) {  // rows of this chunk times sqrt(alpha)
+                scale_rows<B>(th_of(bi), th_of(bi) + C::TILE, sal + bi * CH, cnt, lane);
+                __syncwarp();
+            }
             const int ksteps = (cnt + 15) >> 4;
             const int mj = lane >> 3, mr = lane & 7;
             for (int ks = 0; ks < ksteps; ++ks) {
@@ -328,6 +372,13 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
             if (lane < clast) {
                 const int64_t s = tk.begin + (int64_t)(nch - 1) * CH + lane;
                 qlast = PERM ? (int64_t)a.pos[s] : s;
+                if (HAS_A) cB = a.idx[s];
+            }
+            if (HAS_A) {  // the staged last chunk was scaled: gather it again, unscaled
+                gather_hilo<B>(th_of(0), th_of(0) + C::TILE, a, cB, clast, lane);
+                cp_async_commit();
+                cp_async_wait_all();
+                __syncwarp();
             }
             auto meta2 = [&](int j) {  // chunks before the last are full
                 const int64_t s = tk.begin + (int64_t)j * CH + lane;
@@ -369,7 +420,7 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
     }
 }
 
-template <int B, bool PERM>
+template <int B, bool PERM, bool HAS_A>
 cudaError_t launch_sparse_bf16_all(const StepArgs &a, cudaStream_t s) {
     using C = BfCfg<B>;
     using T = TileCfg<B>;
@@ -377,11 +428,11 @@ cudaError_t launch_sparse_bf16_all(const StepArgs &a, cudaStream_t s) {
     static int per_sm = 0;
     if (!attr_done) {
         cudaError_t e;
-        if ((e = cudaFuncSetAttribute(k_sparse_bf16<B, PERM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if ((e = cudaFuncSetAttribute(k_sparse_bf16<B, PERM, HAS_A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       C::SMEM_BYTES)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(k_split_solve<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       split_solve_smem<B>())) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sparse_bf16<B, PERM>,
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sparse_bf16<B, PERM, HAS_A>,
                                                                C::WARPS * 32, C::SMEM_BYTES)) != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         attr_done = true;
@@ -391,7 +442,7 @@ cudaError_t launch_sparse_bf16_all(const StepArgs &a, cudaStream_t s) {
         const int need = (a.n_tasks + C::WARPS - 1) / C::WARPS;
         if (grid > need) grid = need;
         prof_mark(a.prof, K_SPARSE, s);
-        k_sparse_bf16<B, PERM><<<grid, C::WARPS * 32, C::SMEM_BYTES, s>>>(a);
+        k_sparse_bf16<B, PERM, HAS_A><<<grid, C::WARPS * 32, C::SMEM_BYTES, s>>>(a);
         prof_mark(a.prof, -1, s);
     }
     if (a.n_split > 0) {
@@ -405,7 +456,7 @@ cudaError_t launch_sparse_bf16_all(const StepArgs &a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     prof_mark(a.prof, K_RETRY, s);
-    k_retry<B, PERM, false><<<38, 128, 0, s>>>(a);
+    k_retry<B, PERM, HAS_A><<<38, 128, 0, s>>>(a);
     prof_mark(a.prof, -1, s);
     return cudaGetLastError();
 }

@@ -3,6 +3,7 @@
 
 namespace ials {
 cudaError_t launch_sparse_bf16_b16(const StepArgs &a, cudaStream_t s) {
-    return a.pos ? launch_sparse_bf16_all<16, true>(a, s) : launch_sparse_bf16_all<16, false>(a, s);
+    if (a.alpha) return a.pos ? launch_sparse_bf16_all<16, true, true>(a, s) : launch_sparse_bf16_all<16, false, true>(a, s);
+    return a.pos ? launch_sparse_bf16_all<16, true, false>(a, s) : launch_sparse_bf16_all<16, false, false>(a, s);
 }
 }  // namespace ials

@@ -6,6 +6,7 @@
 namespace ials {
 cudaError_t launch_sparse_bf16_b64(const StepArgs &a, cudaStream_t s) {
     if (a.direct) return launch_sparse_cta_bf16_dispatch<64>(a, s);
+    if (a.alpha) return a.pos ? launch_sparse_gj64_all<true, true, true>(a, s) : launch_sparse_gj64_all<false, true, true>(a, s);
     return a.pos ? launch_sparse_gj64_all<true, false, true>(a, s) : launch_sparse_gj64_all<false, false, true>(a, s);
 }
 }  // namespace ials

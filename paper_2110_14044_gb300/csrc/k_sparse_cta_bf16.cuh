@@ -35,7 +35,7 @@ struct CtaBfCfg {
     static constexpr int BUF = 2 * TILE;    // one staging buffer: hi tile, then lo tile
     static constexpr int SM = B + 4;        // float row stride of the shared matrix (= 4 mod 32)
     static constexpr int M_FLOATS = (B + 1) * SM;
-    static constexpr int SMEM_BYTES = 2 * BUF * 2 + (M_FLOATS + B) * 4 + 16;
+    static constexpr int SMEM_BYTES = 2 * BUF * 2 + (M_FLOATS + B) * 4 + 16 + 2 * CH * 4;  // + sqrt(alpha) per staged row
     static_assert(M_FLOATS >= 2 * RegChol<B>::PANEL, "the panels reuse M");
     static_assert(THREADS >= RegChol<B>::NTL, "one tile per thread");
 };
@@ -217,7 +217,7 @@ __device__ __forceinline__ void cta_bf_gather(const StepArgs &a, int64_t s0, int
     }
 }
 
-template <int B, bool PERM, bool DIRECT>
+template <int B, bool PERM, bool DIRECT, bool HAS_A>
 __global__ void __launch_bounds__(CtaBfCfg<B>::THREADS, 2) k_sparse_cta_bf16(const StepArgs a) {
     using C = CtaBfCfg<B>;
     constexpr int SBH = C::SBH, CH = C::CH, SM = C::SM, NPT = C::NPT;
@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(CtaBfCfg<B>::THREADS, 2) k_sparse_cta_bf16(con
     float *M = reinterpret_cast<float *>(bufs + 2 * C::BUF);
     float *xv = M + C::M_FLOATS;
     int *flag = reinterpret_cast<int *>(xv + B);  // [0] next task, [1] bad pivot
+    float *sal = reinterpret_cast<float *>(flag + 4);  // weighted data: sqrt(alpha) of staged row k in buffer bi
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x, nw = nt >> 5;
     const bool own = tid < RegChol<B>::NTL;
     int ti = 0, tj = 0;
@@ -266,7 +267,12 @@ __global__ void __launch_bounds__(CtaBfCfg<B>::THREADS, 2) k_sparse_cta_bf16(con
                 if (r < cnt) {
                     const int64_t s = tk.begin + (int64_t)j * CH + r;
                     const int64_t q = PERM ? (int64_t)a.pos[s] : s;
-                    const float e = DIRECT ? (a.y ? a.y[q] : 1.f) : a.e[q];
+                    float e = DIRECT ? (a.y ? a.y[q] : 1.f) : a.e[q];
+                    if (HAS_A) {  // weighted data: row and residual (label) times sqrt(alpha)
+                        const float sa = sqrtf(a.alpha[q]);
+                        sal[bi * CH + r] = sa;
+                        e *= sa;
+                    }
                     const __nv_bfloat16 h = __float2bfloat16_rn(e);
                     th[r * SBH + B] = h;
                     tl[r * SBH + B] = __float2bfloat16_rn(e - __bfloat162float(h));
@@ -289,6 +295,33 @@ __global__ void __launch_bounds__(CtaBfCfg<B>::THREADS, 2) k_sparse_cta_bf16(con
             if (ch + 1 < nch) issue(ch + 1, bi ^ 1);
             const int cnt = min(CH, tk.len - ch * CH);
             const __nv_bfloat16 *th = bufs + bi * C::BUF, *tl = th + C::TILE;
+            if (HAS_A) {  // eight threads per staged row, B / 8 values each
+                __nv_bfloat16 *wh = bufs + bi * C::BUF, *wl = wh + C::TILE;
+                for (int t = tid; t < cnt * 8; t += nt) {
+                    const int rr = t >> 3, part = t & 7;
+                    const float sa = sal[bi * CH + rr];
+#pragma unroll
+                    for (int v = 0; v < B / 64; ++v) {
+                        uint4 *ph = reinterpret_cast<uint4 *>(wh + rr * SBH + part * (B / 8)) + v;
+                        uint4 *pl = reinterpret_cast<uint4 *>(wl + rr * SBH + part * (B / 8)) + v;
+                        uint4 hv = *ph, lv = *pl;
+                        __nv_bfloat162 *h2 = reinterpret_cast<__nv_bfloat162 *>(&hv);
+                        __nv_bfloat162 *l2 = reinterpret_cast<__nv_bfloat162 *>(&lv);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float2 hf = __bfloat1622float2(h2[q]), lf = __bfloat1622float2(l2[q]);
+                            const float x0 = (hf.x + lf.x) * sa, x1 = (hf.y + lf.y) * sa;
+                            const __nv_bfloat162 nh = __floats2bfloat162_rn(x0, x1);
+                            const float2 nhf = __bfloat1622float2(nh);
+                            h2[q] = nh;
+                            l2[q] = __floats2bfloat162_rn(x0 - nhf.x, x1 - nhf.y);
+                        }
+                        *ph = hv;
+                        *pl = lv;
+                    }
+                }
+                __syncthreads();
+            }
             const int ksteps = (cnt + 15) >> 4;
             for (int ks = 0; ks < ksteps; ++ks) cta_bf_kstep_any<B>(warp, acc, gac, th, tl, ks, lane);
         }
@@ -359,6 +392,17 @@ __global__ void __launch_bounds__(CtaBfCfg<B>::THREADS, 2) k_sparse_cta_bf16(con
                 }
             }
         };
+        if (HAS_A) {  // the staged chunks were scaled: every chunk is gathered again, unscaled
+            for (int ch = 0; ch < nch; ++ch) {
+                __syncthreads();
+                cta_bf_gather<B>(a, tk.begin + (int64_t)ch * CH, min(CH, tk.len - ch * CH), bufs, bufs + C::TILE);
+                cp_async_commit();
+                cp_async_wait_all();
+                __syncthreads();
+                process(ch, bufs);
+            }
+            continue;
+        }
         for (int ch = nch - 1; ch >= 0 && ch >= nch - 2; --ch) process(ch, bufs + (ch & 1) * C::BUF);
         if (nch > 2) {
             __syncthreads();  // the staged chunks are consumed before they are overwritten
@@ -381,7 +425,7 @@ __global__ void __launch_bounds__(CtaBfCfg<B>::THREADS, 2) k_sparse_cta_bf16(con
 // Whole sparse part of a BF16 block-side step at B = 64, 128: the CTA kernel,
 // then long rows (slot sums and the register-tile solve), their residual
 // update (not for DIRECT), FP64 retry.
-template <int B, bool PERM, bool DIRECT>
+template <int B, bool PERM, bool DIRECT, bool HAS_A>
 cudaError_t launch_sparse_cta_bf16_all(const StepArgs &a, cudaStream_t s) {
     using C = CtaBfCfg<B>;
     using CF = CtaCfg<B>;
@@ -389,13 +433,13 @@ cudaError_t launch_sparse_cta_bf16_all(const StepArgs &a, cudaStream_t s) {
     static int per_sm = 0;
     if (!attr_done) {
         cudaError_t e;
-        if ((e = cudaFuncSetAttribute(k_sparse_cta_bf16<B, PERM, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if ((e = cudaFuncSetAttribute(k_sparse_cta_bf16<B, PERM, DIRECT, HAS_A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       C::SMEM_BYTES)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(k_split_solve_rc<B, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       RcCfg<B>::SMEM_BYTES)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_retry_cta<B, PERM, false, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if ((e = cudaFuncSetAttribute(k_retry_cta<B, PERM, HAS_A, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       retry_cta_smem<B>())) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sparse_cta_bf16<B, PERM, DIRECT>, C::THREADS,
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sparse_cta_bf16<B, PERM, DIRECT, HAS_A>, C::THREADS,
                                                                C::SMEM_BYTES)) != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         attr_done = true;
@@ -404,7 +448,7 @@ cudaError_t launch_sparse_cta_bf16_all(const StepArgs &a, cudaStream_t s) {
         int grid = 152 * per_sm;
         if (grid > a.n_tasks) grid = a.n_tasks;
         prof_mark(a.prof, K_SPARSE, s);
-        k_sparse_cta_bf16<B, PERM, DIRECT><<<grid, C::THREADS, C::SMEM_BYTES, s>>>(a);
+        k_sparse_cta_bf16<B, PERM, DIRECT, HAS_A><<<grid, C::THREADS, C::SMEM_BYTES, s>>>(a);
         prof_mark(a.prof, -1, s);
     }
     if (a.n_split > 0) {
@@ -418,15 +462,23 @@ cudaError_t launch_sparse_cta_bf16_all(const StepArgs &a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     prof_mark(a.prof, K_RETRY, s);
-    k_retry_cta<B, PERM, false, DIRECT><<<76, CF::THREADS, retry_cta_smem<B>(), s>>>(a);
+    k_retry_cta<B, PERM, HAS_A, DIRECT><<<76, CF::THREADS, retry_cta_smem<B>(), s>>>(a);
     prof_mark(a.prof, -1, s);
     return cudaGetLastError();
 }
 
+template <int B, bool HAS_A>
+cudaError_t launch_sparse_cta_bf16_weights(const StepArgs &a, cudaStream_t s) {
+    if (a.direct)
+        return a.pos ? launch_sparse_cta_bf16_all<B, true, true, HAS_A>(a, s)
+                     : launch_sparse_cta_bf16_all<B, false, true, HAS_A>(a, s);
+    return a.pos ? launch_sparse_cta_bf16_all<B, true, false, HAS_A>(a, s)
+                 : launch_sparse_cta_bf16_all<B, false, false, HAS_A>(a, s);
+}
+
 template <int B>
 cudaError_t launch_sparse_cta_bf16_dispatch(const StepArgs &a, cudaStream_t s) {
-    if (a.direct) return a.pos ? launch_sparse_cta_bf16_all<B, true, true>(a, s) : launch_sparse_cta_bf16_all<B, false, true>(a, s);
-    return a.pos ? launch_sparse_cta_bf16_all<B, true, false>(a, s) : launch_sparse_cta_bf16_all<B, false, false>(a, s);
+    return a.alpha ? launch_sparse_cta_bf16_weights<B, true>(a, s) : launch_sparse_cta_bf16_weights<B, false>(a, s);
 }
 
 }  // namespace ials

@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(Gj64::THREADS, 1) k_sparse_gj64(const StepArgs
 // k_sparse_cta_bf16.cuh) with the batched warp solves.  The residuals arrive
 // as floats and are split into the hi / lo residual column of the staged tile
 // before the products.
-template <bool PERM>
+template <bool PERM, bool HAS_A>
 __global__ void __launch_bounds__(Gj64::THREADS, 2) k_sparse_gj64_bf16(const StepArgs a) {
     using C = Gj64;
     using CBf = CtaBfCfg<64>;
@@ -549,6 +549,7 @@ __global__ void __launch_bounds__(Gj64::THREADS, 2) k_sparse_gj64_bf16(const Ste
             if (tid < cnt) {
                 const int64_t q = PERM ? (int64_t)S.cq[ib * CH + tid] : tks[r].begin + (int64_t)c * CH + tid;
                 cp_async4(S.she + sb * CH + tid, a.e + q);
+                if (HAS_A) cp_async4(S.sha + sb * CH + tid, a.alpha + q);
             }
         };
         auto body = [&](int j, int sb, int ib) {
@@ -568,8 +569,30 @@ __global__ void __launch_bounds__(Gj64::THREADS, 2) k_sparse_gj64_bf16(const Ste
                 if (tk.slot < 0 && warp < CBf::WARPS) cta_bf_init_any<B>(warp, acc, gac, a, tk.row, lam, lane);
             }
             __nv_bfloat16 *th = reinterpret_cast<__nv_bfloat16 *>(S.stage + sb * C::STAGE), *tl = th + CBf::TILE;
-            if (tid < cnt) {  // residual column: hi / lo split
-                const float e = S.she[sb * CH + tid];
+            if (tid < cnt) {  // residual column: hi / lo split (weighted: row and residual times sqrt(alpha))
+                float e = S.she[sb * CH + tid];
+                if (HAS_A) {
+                    const float sa = sqrtf(S.sha[sb * CH + tid]);
+                    e *= sa;
+#pragma unroll
+                    for (int v = 0; v < B / 8; ++v) {
+                        uint4 hv = reinterpret_cast<uint4 *>(th + tid * SBH)[v];
+                        uint4 lv = reinterpret_cast<uint4 *>(tl + tid * SBH)[v];
+                        __nv_bfloat162 *h2 = reinterpret_cast<__nv_bfloat162 *>(&hv);
+                        __nv_bfloat162 *l2 = reinterpret_cast<__nv_bfloat162 *>(&lv);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float2 hf = __bfloat1622float2(h2[q]), lf = __bfloat1622float2(l2[q]);
+                            const float x0 = (hf.x + lf.x) * sa, x1 = (hf.y + lf.y) * sa;
+                            const __nv_bfloat162 nh = __floats2bfloat162_rn(x0, x1);
+                            const float2 nhf = __bfloat1622float2(nh);
+                            h2[q] = nh;
+                            l2[q] = __floats2bfloat162_rn(x0 - nhf.x, x1 - nhf.y);
+                        }
+                        reinterpret_cast<uint4 *>(th + tid * SBH)[v] = hv;
+                        reinterpret_cast<uint4 *>(tl + tid * SBH)[v] = lv;
+                    }
+                }
                 const __nv_bfloat16 h = __float2bfloat16_rn(e);
                 th[tid * SBH + B] = h;
                 tl[tid * SBH + B] = __float2bfloat16_rn(e - __bfloat162float(h));
@@ -602,7 +625,7 @@ cudaError_t launch_sparse_gj64_all(const StepArgs &a, cudaStream_t s) {
     using CF = CtaCfg<64>;
     static bool attr_done = false;
     static int per_sm = 0;
-    auto kern = BF ? (void (*)(const StepArgs))k_sparse_gj64_bf16<PERM> : (void (*)(const StepArgs))k_sparse_gj64<PERM, HAS_A>;
+    auto kern = BF ? (void (*)(const StepArgs))k_sparse_gj64_bf16<PERM, HAS_A> : (void (*)(const StepArgs))k_sparse_gj64<PERM, HAS_A>;
     if (!attr_done) {
         cudaError_t e;
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES)) != cudaSuccess)

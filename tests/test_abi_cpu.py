@@ -67,7 +67,7 @@ def _create(p, n_users, n_items, uptr, uidx, **kw):
     return _abi.ials_create(p, n_users, n_items, np.asarray(uptr, np.int64), np.asarray(uidx, np.int32), **kw)
 
 
-@pytest.mark.parametrize("case", ["d", "b_not_dividing", "bf16_b", "bf16_weighted", "alpha0",
+@pytest.mark.parametrize("case", ["d", "b_not_dividing", "bf16_b", "alpha0",
                                   "indptr_end", "indptr_order", "item_range", "repeat",
                                   "transpose_len", "transpose_pairs", "alpha_zero", "y_nan"])
 def test_create_validates_on_the_host(case):
@@ -84,9 +84,6 @@ def test_create_validates_on_the_host(case):
         good["p"] = _abi.make_params(16, 32, 0.1, 0.01)
     elif case == "bf16_b":
         good["p"] = _abi.make_params(16, 8, 0.1, 0.01, precision=bf16)
-    elif case == "bf16_weighted":
-        good["p"] = _abi.make_params(32, 16, 0.1, 0.01, precision=bf16)
-        kw["alpha"] = np.ones(5, np.float32)
     elif case == "alpha0":
         good["p"] = _abi.make_params(16, 8, -0.1, 0.01)
     elif case == "indptr_end":
@@ -120,12 +117,13 @@ def test_create_accepts_valid_input_up_to_the_device_check():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
         pytest.skip("a device is present")
-    p = _abi.make_params(16, 8, 0.1, 0.01)
-    with pytest.raises(_abi.IalsError) as ei:
-        _create(p, 3, 4, [0, 2, 3, 5], [0, 1, 3, 1, 2],
-                i_indptr=np.array([0, 1, 3, 4, 5], np.int64), i_users=np.array([0, 2, 0, 2, 1], np.int32),
-                y=np.ones(5, np.float32), alpha=np.full(5, 2.0, np.float32))
-    assert ei.value.status == _abi.ECUDA, str(ei.value)
+    for p in (_abi.make_params(16, 8, 0.1, 0.01),
+              _abi.make_params(32, 16, 0.1, 0.01, precision=_abi.PREC_BF16)):  # weights in BF16 too
+        with pytest.raises(_abi.IalsError) as ei:
+            _create(p, 3, 4, [0, 2, 3, 5], [0, 1, 3, 1, 2],
+                    i_indptr=np.array([0, 1, 3, 4, 5], np.int64), i_users=np.array([0, 2, 0, 2, 1], np.int32),
+                    y=np.ones(5, np.float32), alpha=np.full(5, 2.0, np.float32))
+        assert ei.value.status == _abi.ECUDA, str(ei.value)
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -145,8 +145,8 @@ def test_bf16_rejects_unsupported_inputs():
         Model(prob.data, 32, 8, 0.1, 1e-3)   # b = 8
     with pytest.raises(_abi.IalsError):
         Model(prob.data, 36, 4, 0.1, 1e-3)   # b = 4, d % 8 != 0
-    with pytest.raises(_abi.IalsError):
-        Model(prob.data, 32, 16, 0.1, 1e-3, alpha=np.ones(prob.data.nnz, np.float32))
+    # weighted data is supported on this path (test_bf16_weighted_*)
+    Model(prob.data, 32, 16, 0.1, 1e-3, alpha=np.ones(prob.data.nnz, np.float32)).close()
 
 
 @pytest.mark.parametrize("n,d,p0,bs", [(1, 8, 0, 16), (64, 128, 32, 32), (1000, 64, 48, 16),
@@ -195,3 +195,55 @@ def test_msd_shaped_subsample_bf16_b128_sampled_rows():
         err = np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-12)
         print(f"side {side}: max row rel err {err.max():.2e}")
         assert err.max() <= 1e-3, (side, err.max())
+
+
+@pytest.mark.parametrize("b", [16, 32, 64, 128])
+def test_bf16_weighted_block_steps(b):
+    """General (y, alpha) data on the BF16 pattern: rows scaled by sqrt(alpha) before
+    the compensated products; single block steps against the oracle."""
+    d = 64 if b <= 32 else 128
+    prob = synth.preset("parity_2k", seed=50 + b, n_users=300, n_items=200, nnz=6000, len_max=200, d=d)
+    data = prob.data
+    rng = np.random.default_rng(b)
+    y = rng.uniform(0.5, 2.0, data.nnz).astype(np.float32)
+    al = rng.uniform(0.5, 3.0, data.nnz).astype(np.float32)
+    m = Model(data, d, b, 0.1, 2e-3, 0.3, W0=prob.W0, H0=prob.H0, y=y, alpha=al)
+    P = oracle.Problem.from_data(data, d, b, 0.1, 2e-3, 0.3, y=y, alpha=al)
+    W, H = P.factors(prob.W0, prob.H0)
+    yhat = oracle.predict(P, W, H)
+    for k in range(min(2, d // b)):
+        for side in (0, 1):
+            assert m.block_step(side, k) == 0
+            oracle.halfstep(P, side, k, W, H, yhat)
+            Wg, Hg = m.factors()
+            assert rel_embed_err(Wg, W) <= 1e-3 and rel_embed_err(Hg, H) <= 1e-3, (k, side)
+    e = m.residuals().astype(np.float64)
+    ref_e = yhat - y.astype(np.float64)
+    assert np.abs(e - ref_e).max() <= 1e-3 * np.abs(ref_e).max()
+
+
+@pytest.mark.parametrize("d,b", [(32, 32), (128, 64), (128, 128)])
+def test_bf16_weighted_epochs_with_long_rows(d, b):
+    """Weighted epochs with rows long enough to be cut into chunks, against the
+    oracle's objective (1e-3) and embeddings."""
+    n_users, n_items = 700, 600
+    rng = np.random.default_rng(60 + b)
+    mask = rng.random((n_users, n_items)) < 0.03
+    mask[5, :] = True
+    mask[:, 7] = True
+    u, i = np.nonzero(mask)
+    data = synth.from_pairs(n_users, n_items, u, i)
+    W0, H0 = synth.init_factors(n_users, n_items, d, 0.1 / np.sqrt(d), 6)
+    y = rng.uniform(0.5, 2.0, data.nnz).astype(np.float32)
+    al = rng.uniform(0.5, 3.0, data.nnz).astype(np.float32)
+    m = Model(data, d, b, 0.1, 1e-3, 0.2, W0=W0, H0=H0, y=y, alpha=al, graph=True)
+    o, st = m.epoch(2, objective=True)
+    assert st == 0
+    P = oracle.Problem.from_data(data, d, b, 0.1, 1e-3, 0.2, y=y, alpha=al)
+    Wr, Hr, _, _, _ = oracle.ialspp(P, 2, W0, H0) if b < d else (*oracle.ials(P, 2, W0, H0)[:2], None, None, None)
+    ref = oracle.objective(P, Wr, Hr)
+    W, H = m.factors()
+    print(f"bf16 weighted d={d} b={b}: rel objective {abs(o - ref) / ref:.2e}, "
+          f"embedding W {rel_embed_err(W, Wr):.2e} H {rel_embed_err(H, Hr):.2e}")
+    assert abs(o - ref) <= BF16_OBJ_TOL * ref
+    assert rel_embed_err(W, Wr) <= 5e-2 and rel_embed_err(H, Hr) <= 5e-2
