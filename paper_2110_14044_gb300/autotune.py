@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _abi
 
-CANDIDATES = (1, 2, 4, 8, 16, 32, 64, 128)  # b = 1 is iCD (Alg. 2); b = d is iALS (Alg. 1)
+CANDIDATES = (1, 2, 4, 8, 16, 32, 64, 128, 256)  # b = 1 is iCD (Alg. 2); b = d is iALS (Alg. 1)
 
 
 def admissible(d: int, b: int, precision: int) -> bool:
@@ -25,7 +25,7 @@ def admissible(d: int, b: int, precision: int) -> bool:
         return False
     if precision == _abi.PREC_BF16:
         return b in (16, 32, 64, 128) and d % 8 == 0
-    return b in (1, 2, 4, 8, 16, 32, 64, 128)
+    return b in (1, 2, 4, 8, 16, 32, 64, 128, 256)
 
 
 def autotune_block_size(data, d, alpha0, lam, nu=0.0, precision=_abi.PREC_FP32,

@@ -102,7 +102,7 @@ struct SideDev {
 };
 
 bool valid_block(int b) {
-    return b == 1 || b == 2 || b == 4 || b == 8 || b == 16 || b == 32 || b == 64 || b == 128;
+    return b == 1 || b == 2 || b == 4 || b == 8 || b == 16 || b == 32 || b == 64 || b == 128 || b == 256;
 }
 
 cudaError_t launch_sparse(const StepArgs &a, cudaStream_t s) {
@@ -115,6 +115,7 @@ cudaError_t launch_sparse(const StepArgs &a, cudaStream_t s) {
         case 32: return launch_sparse_b32(a, s);
         case 64: return launch_sparse_b64(a, s);
         case 128: return launch_sparse_b128(a, s);
+        case 256: return launch_sparse_b256(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -142,6 +143,7 @@ struct ials_ctx {
     double *obj_part = nullptr;
     int32_t n_obj_part = 0;
     double *g64a = nullptr, *g64b = nullptr, *g64ws = nullptr;
+    double *retry_ws = nullptr;  // b > 128: FP64 re-solve systems
     // iCD path (b = 1): Gramian columns (two of d), their partials, completion counter
     float *icd_g = nullptr, *icd_gpart = nullptr;
     float *WT = nullptr, *HT = nullptr;  // transposed factors (d x n), kept current by the passes
@@ -289,6 +291,7 @@ StepArgs step_args(ials_ctx *c, int side, int p0, Profiler *prof) {
     a.retry = c->ctl + 1;
     a.stats = c->stats;
     a.force_fp64 = (c->p.flags & IALS_FLAG_FORCE_FP64) ? 1 : 0;
+    a.retry_ws = c->retry_ws;
     a.prof = prof;
     a.Xh = side == 0 ? c->Wh : c->Hh;
     a.Xl = side == 0 ? c->Wl : c->Hl;
@@ -339,7 +342,7 @@ ials_status icd_pass_enqueue(ials_ctx *c, int side, int f, int fn, const float *
 
 // The iALS path (Algorithm 1) runs for b = d in {64, 128} unless the general path is forced.
 bool use_ials(const ials_ctx *c) {
-    return c->p.b == c->p.d && (c->p.b == 64 || c->p.b == 128) && !(c->p.flags & IALS_FLAG_GENERAL);
+    return c->p.b == c->p.d && c->p.b >= 64 && !(c->p.flags & IALS_FLAG_GENERAL);
 }
 
 // One iALS epoch (Algorithm 1): per side the full Gramian G of the fixed side,
@@ -514,7 +517,7 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     const ials_params p = *params;
     if (p.d < 4 || p.d > 4096 || p.d % 4 != 0) return fail(IALS_EINVAL, "d must be a multiple of 4 in [4, 4096]");
     if (!valid_block(p.b) || p.d % p.b != 0)
-        return fail(IALS_EINVAL, "b must be a power of two <= 128 that divides d");
+        return fail(IALS_EINVAL, "b must be a power of two <= 256 that divides d");
     if (!(p.alpha0 >= 0) || !(p.lambda >= 0) || !(p.nu >= 0) || !std::isfinite(p.alpha0) ||
         !std::isfinite(p.lambda) || !std::isfinite(p.nu))
         return fail(IALS_EINVAL, "alpha0, lambda, nu must be finite and >= 0");
@@ -682,6 +685,7 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
         ALLOC(c->icd_xold, max_split, "long-row coordinates");
         ALLOC(c->icd_done, 1, "completion counter");
     }
+    if (sparse_retry_ws_doubles(b) > 0) ALLOC(c->retry_ws, sparse_retry_ws_doubles(b), "FP64 re-solve workspace");
     ALLOC(c->g64a, (int64_t)d * d, "FP64 Gramian");
     ALLOC(c->g64b, (int64_t)d * d, "FP64 Gramian");
     ALLOC(c->g64ws, std::max(gram64_ws_doubles(n_users, d), gram64_ws_doubles(n_items, d)),

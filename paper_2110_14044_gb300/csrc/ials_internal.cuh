@@ -116,6 +116,7 @@ struct StepArgs {
     int64_t *stats;         // [0] = FP64 retries, [1] = not positive definite
     int32_t force_fp64;     // fault injection: every FP32 pivot counts as failed
     int32_t direct;         // b = d (Algorithm 1): solve for x_r itself from sum alpha y f, no residuals
+    double *retry_ws;       // b > 128: FP64 systems of the re-solve kernel's blocks
     Profiler *prof;         // host only: event marks around launches, or nullptr
 };
 
@@ -260,9 +261,12 @@ cudaError_t launch_sparse_b4(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_sparse_b8(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_sparse_b16(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_sparse_b32(const StepArgs &a, cudaStream_t s);
-// block sizes 64 and 128 (k_sparse_b64.cu, k_sparse_b128.cu): one CTA per task
+// block sizes 64, 128 and 256 (k_sparse_b64.cu, k_sparse_b128.cu, k_sparse_b256.cu)
 cudaError_t launch_sparse_b64(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_sparse_b128(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_sparse_b256(const StepArgs &a, cudaStream_t s);
+// doubles of FP64 re-solve workspace a block size needs (0 up to b = 128)
+int64_t sparse_retry_ws_doubles(int32_t b);
 // fold-in (k_foldin.cu): one CTA per request, or (cluster) one cluster of
 // kFoldCluster CTAs per request; factors per request: foldin_factor_floats
 cudaError_t launch_foldin(const FoldArgs &a, bool cluster, cudaStream_t s);

@@ -15,7 +15,7 @@ template <int B>
 struct CtaCfg {
     static constexpr int NB = B / 8;
     static constexpr int NTL = NB * (NB + 1) / 2;
-    static constexpr int NG = B == 64 ? 7 : 2;
+    static constexpr int NG = B == 64 ? 7 : (B == 128 ? 2 : 1);
     static constexpr int ACTIVE = NTL * NG;
     static constexpr int THREADS = (ACTIVE + 31) / 32 * 32;
     static constexpr int SB = B + 4;   // row stride of staging buffers and of M
@@ -429,14 +429,20 @@ __device__ void cta_residual_update2(const StepArgs &a, int64_t s0, int len, int
 // FP64 re-solve of queued rows: statistics accumulated from scratch in FP64 by
 // the tile owners (one group, reading slices straight from global memory), the
 // blocked Cholesky in FP64, apply and residual update.
+// Above b = 128 the FP64 system (B + 1)^2 doubles does not fit shared memory;
+// it lives in a per-block slice of a.retry_ws instead.
+template <int B>
+constexpr bool retry_in_global() { return B > 128; }
+
 template <int B, bool PERM, bool HAS_A, bool DIRECT = false>
 __global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_retry_cta(const StepArgs a) {
     using C = CtaCfg<B>;
     constexpr int SM = B + 1;
     extern __shared__ float4 smem4[];
     float *buf = reinterpret_cast<float *>(smem4);  // CH x SB staging for the residual update
-    double *M = reinterpret_cast<double *>(buf + C::BUF);  // (B+1) x (B+1)
-    double *diag0 = M + (B + 1) * SM;
+    double *sm_after = reinterpret_cast<double *>(buf + C::BUF);
+    double *M = retry_in_global<B>() ? a.retry_ws + (int64_t)blockIdx.x * (B + 1) * SM : sm_after;
+    double *diag0 = retry_in_global<B>() ? sm_after : M + (B + 1) * SM;
     double *invd = diag0 + B;
     double *xd = invd + B;
     int *flag = reinterpret_cast<int *>(xd + B);
@@ -509,7 +515,11 @@ __global__ void __launch_bounds__(CtaCfg<B>::THREADS) k_retry_cta(const StepArgs
 
 template <int B>
 constexpr int retry_cta_smem() {
-    return CtaCfg<B>::BUF * 4 + ((B + 1) * (B + 1) + 3 * B) * 8 + 16 + B * 4;
+    return CtaCfg<B>::BUF * 4 + ((retry_in_global<B>() ? 0 : (B + 1) * (B + 1)) + 3 * B) * 8 + 16 + B * 4;
 }
+// Blocks of the FP64 re-solve kernel, and its global workspace (doubles) above b = 128.
+constexpr int kRetryBlocks = 76;
+template <int B>
+constexpr int64_t retry_ws_doubles() { return retry_in_global<B>() ? (int64_t)kRetryBlocks * (B + 1) * (B + 1) : 0; }
 
 }  // namespace ials

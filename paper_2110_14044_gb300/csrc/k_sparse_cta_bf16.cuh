@@ -462,7 +462,7 @@ cudaError_t launch_sparse_cta_bf16_all(const StepArgs &a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     prof_mark(a.prof, K_RETRY, s);
-    k_retry_cta<B, PERM, HAS_A, DIRECT><<<76, CF::THREADS, retry_cta_smem<B>(), s>>>(a);
+    k_retry_cta<B, PERM, HAS_A, DIRECT><<<kRetryBlocks, CF::THREADS, retry_cta_smem<B>(), s>>>(a);
     prof_mark(a.prof, -1, s);
     return cudaGetLastError();
 }

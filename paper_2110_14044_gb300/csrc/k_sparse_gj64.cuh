@@ -659,7 +659,7 @@ cudaError_t launch_sparse_gj64_all(const StepArgs &a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     prof_mark(a.prof, K_RETRY, s);
-    k_retry_cta<64, PERM, HAS_A, false><<<76, CF::THREADS, retry_cta_smem<64>(), s>>>(a);
+    k_retry_cta<64, PERM, HAS_A, false><<<kRetryBlocks, CF::THREADS, retry_cta_smem<64>(), s>>>(a);
     prof_mark(a.prof, -1, s);
     return cudaGetLastError();
 }

@@ -182,7 +182,8 @@ struct RcCfg {
     static constexpr int NG = B == 64 ? 2 : 1;
     static constexpr int ACTIVE = R::NTL * NG;
     static constexpr int THREADS = (ACTIVE + 31) / 32 * 32;
-    static constexpr int MINB = B == 64 ? 5 : 3;     // resident CTAs per SM (caps registers at ~136)
+    // resident CTAs per SM (caps registers at ~136; b = 256: 544 threads, one CTA)
+    static constexpr int MINB = B == 64 ? 5 : (B == 128 ? 3 : 1);
     static constexpr int SB = CtaCfg<B>::SB, CH = CtaCfg<B>::CH, BUF = CtaCfg<B>::BUF;
     static constexpr int RED = (NG - 1) * R::NTL * 72;  // group partials (tile + gradient block)
     // floats: staging, e[2][CH], alpha[2][CH], group partials, two panels, zv, flags
@@ -474,7 +475,7 @@ cudaError_t launch_sparse_rc_all(const StepArgs &a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     prof_mark(a.prof, K_RETRY, s);
-    k_retry_cta<B, PERM, HAS_A, DIRECT><<<76, CF::THREADS, retry_cta_smem<B>(), s>>>(a);
+    k_retry_cta<B, PERM, HAS_A, DIRECT><<<kRetryBlocks, CF::THREADS, retry_cta_smem<B>(), s>>>(a);
     prof_mark(a.prof, -1, s);
     return cudaGetLastError();
 }

@@ -500,3 +500,75 @@ def test_profile_and_work_model_hooks():
     assert work["sparse"][0] == pytest.approx(nb * (nnz * per_nz + rows * per_row), rel=1e-12)
     # Gramian FLOPs: 2 |fixed| d b per half-step (Eq. 10)
     assert work["gram"][1] == pytest.approx(nb * 2 * (n_items + n_users) * d * b, rel=1e-12)
+
+
+# --------------------------------------------------------- block size 256 (FP32)
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_block_size_256_steps_and_epochs(weighted):
+    """b = 256 (d = 512): single block steps against the oracle, then an epoch with
+    rows long enough to be cut into chunks (split-row path) against the oracle."""
+    d, b = 512, 256
+    n_users, n_items = 1200, 1000  # more rows than d on both sides: well-conditioned Gramians
+    rng = np.random.default_rng(70 + weighted)
+    mask = rng.random((n_users, n_items)) < 0.02
+    mask[5, :] = True   # longer than the chunk length on both sides
+    mask[:, 7] = True
+    u, i = np.nonzero(mask)
+    data = synth.from_pairs(n_users, n_items, u, i)
+    W0, H0 = synth.init_factors(n_users, n_items, d, 0.1 / np.sqrt(d), 7)
+    y, a = weights(data.nnz, 71) if weighted else (None, None)
+    m = Model(data, d, b, 0.1, 2e-3, 0.5, W0=W0, H0=H0, y=y, alpha=a)
+    P = oracle.Problem.from_data(data, d, b, 0.1, 2e-3, 0.5, y=y, alpha=a)
+    W, H = P.factors(W0, H0)
+    yhat = oracle.predict(P, W, H)
+    for k in range(d // b):
+        for side in (0, 1):
+            assert m.block_step(side, k) == 0
+            assert oracle.halfstep(P, side, k, W, H, yhat) == 0
+            Wg, Hg = m.factors()
+            assert rel_embed_err(Wg, W) <= STEP_TOL and rel_embed_err(Hg, H) <= STEP_TOL, (k, side)
+    o, st = m.epoch(1, objective=True)
+    assert st == 0
+    Wr, Hr, _, _, _ = oracle.ialspp(P, 1, W, H)
+    assert abs(o - oracle.objective(P, Wr, Hr)) <= OBJ_TOL * abs(o)
+
+
+def test_block_size_256_fp64_retry_and_ials_path():
+    """Every FP32 pivot treated as failed at b = 256: the FP64 re-solve (its systems
+    in global memory above b = 128) gives the same step; b = d = 256 runs the
+    iALS path (Algorithm 1) and matches the oracle's closed form."""
+    d = 256
+    # more users and items than d, so that the Gramians (and the row systems) are
+    # well conditioned enough for an FP32 comparison
+    prob = small(n_users=1500, n_items=1200, nnz=30000, seed=72, d=d, len_max=400)
+    data = prob.data
+    a = Model(data, d, 256, 0.1, 1e-3, W0=prob.W0, H0=prob.H0, general=True)
+    f = Model(data, d, 256, 0.1, 1e-3, W0=prob.W0, H0=prob.H0, general=True, force_fp64=True)
+    assert a.block_step(0, 0) == 0 and f.block_step(0, 0) == 0
+    retries, not_pd = f.stats()
+    assert retries == data.n_users and not_pd == 0
+    assert rel_embed_err(f.factors()[0], a.factors()[0]) <= STEP_TOL
+    # both half-steps of the general path at b = d against the oracle.  A row with
+    # no interactions has the exact solution 0 here (its row term is its Hessian
+    # times the old row), so the rounding left in it scales with the old row:
+    # errors are measured against the larger of the old and the new row norms.
+    P = oracle.Problem.from_data(data, d, 256, 0.1, 1e-3, 0.0)
+    W, H = P.factors(prob.W0, prob.H0)
+    yhat = oracle.predict(P, W, H)
+    for side in (0, 1):
+        if side == 1:
+            assert a.block_step(1, 0) == 0
+        old = (W if side == 0 else H).copy()
+        assert oracle.halfstep(P, side, 0, W, H, yhat) == 0
+        got, ref = a.factors()[side].astype(np.float64), (W if side == 0 else H)
+        scale = np.maximum(np.linalg.norm(ref, axis=1), np.linalg.norm(old, axis=1))
+        assert np.max(np.linalg.norm(got - ref, axis=1) / scale) <= STEP_TOL, side
+    e = a.residuals().astype(np.float64)
+    assert np.abs(e - (yhat - 1.0)).max() <= STEP_TOL * np.abs(yhat - 1.0).max()
+    m = Model(data, d, d, 0.1, 1e-3, 0.0, W0=prob.W0, H0=prob.H0)
+    m.epoch(1)
+    W, H = m.factors()
+    P = oracle.Problem.from_data(data, d, d, 0.1, 1e-3, 0.0)
+    Wr, Hr, st = oracle.ials(P, 1, prob.W0, prob.H0)
+    assert rel_embed_err(W, Wr) <= EMB_TOL and rel_embed_err(H, Hr) <= EMB_TOL

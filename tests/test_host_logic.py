@@ -19,6 +19,7 @@ def test_admissible_block_sizes():
     assert autotune.admissible(128, 16, bf16) and autotune.admissible(1024, 128, bf16)
     assert not autotune.admissible(128, 8, bf16)
     assert [b for b in autotune.CANDIDATES if autotune.admissible(64, b, fp32)] == [1, 2, 4, 8, 16, 32, 64]
+    assert autotune.admissible(512, 256, fp32) and not autotune.admissible(512, 256, bf16)
     assert [b for b in autotune.CANDIDATES if autotune.admissible(64, b, bf16)] == [16, 32, 64]
 
 
