@@ -349,11 +349,14 @@ def kernel_rooflines(m, steps, prec, b, precision_name, workload_key, peaks):
 # ----------------------------------------------------------------- our arm
 def run_ours(args):
     rank, local_rank, world = env_rank()
-    msd_job = None
-    if rank == 0 and args.d1024 and args.workload == WORKLOAD and not (args.d or args.b):
+    msd_job = sweep_job = None
+    default_run = args.workload == WORKLOAD and not (args.d or args.b)
+    if rank == 0 and args.d1024 and default_run:
         # the d = 1024 workload's interaction set is drawn in a spawned process (no CUDA
         # in it) while the d = 128 measurements run
-        msd_job = start_msd_generation()
+        msd_job = start_generation(MSD)
+    if rank == 0 and args.sweep and default_run:
+        sweep_job = start_generation(SWEEP)
     import torch
     if world > 1:
         import torch.distributed as dist
@@ -484,8 +487,11 @@ def run_ours(args):
         line["d1024"] = run_msd(msd_job, args, stream, peaks)
     if rank == 0 and args.foldin:
         line["foldin"] = run_foldin(cpu_sample=0 if args.no_cpu_baseline else 40)
-    if rank == 0 and args.convergence:
-        line["convergence"] = run_convergence(prob, args.convergence)
+    conv = args.convergence if args.convergence is not None else (6 if default_run else 0)
+    if rank == 0 and conv:
+        line["convergence"] = run_convergence(prob, conv, stream)
+    if sweep_job is not None:
+        line["sweep_skewed"] = run_sweep(sweep_job, stream)
     if rank == 0 and args.autotune:
         from paper_2110_14044_gb300 import autotune
         tuned = {}
@@ -506,22 +512,38 @@ MSD = "msd_570k"
 MSD_BLOCKS = (32, 64, 128)   # the autotuner's candidates at d = 1024 (b = 128 is the stated one)
 
 
-def _draw_msd(out_dir):
-    """Child process: draw the MSD-shaped interaction set and save its CSR views."""
+def _draw_preset(name, out_dir):
+    """Child process: draw a preset's interaction set (seed 0) and save its CSR views."""
     from paper_2110_14044_gb300 import synth
-    c = synth.PRESETS[MSD]
+    c = synth.PRESETS[name]
     data = synth.make_interactions(c["n_users"], c["n_items"], c["nnz"], c["zipf_s"], c["ln_mu"],
-                                   c["ln_sigma"], c["len_min"], c["len_max"], 0)
+                                   c["ln_sigma"], c["len_min"], c["len_max"], 0, c.get("user_zipf"))
     for k in ("u_indptr", "u_items", "i_indptr", "i_users"):
         np.save(os.path.join(out_dir, k + ".npy"), getattr(data, k))
 
 
-def start_msd_generation():
+def start_generation(name):
+    """Draw a preset's interactions in a spawned process (no CUDA in it) while the
+    GPU measures something else; collect with `collect_generation`."""
     import multiprocessing as mp
-    out_dir = tempfile.mkdtemp(prefix="msd_")
-    proc = mp.get_context("spawn").Process(target=_draw_msd, args=(out_dir,))
+    out_dir = tempfile.mkdtemp(prefix=name + "_")
+    proc = mp.get_context("spawn").Process(target=_draw_preset, args=(name, out_dir))
     proc.start()
-    return proc, out_dir
+    return name, proc, out_dir
+
+
+def collect_generation(job):
+    import shutil
+    from paper_2110_14044_gb300 import synth
+    name, proc, out_dir = job
+    proc.join()
+    if proc.exitcode != 0:
+        shutil.rmtree(out_dir, ignore_errors=True)
+        raise RuntimeError(f"generator process for {name} exited with {proc.exitcode}")
+    arrs = {k: np.load(os.path.join(out_dir, k + ".npy")) for k in ("u_indptr", "u_items", "i_indptr", "i_users")}
+    shutil.rmtree(out_dir, ignore_errors=True)
+    c = synth.PRESETS[name]
+    return synth.Interactions(c["n_users"], c["n_items"], **arrs)
 
 
 def run_msd(job, args, stream, peaks):
@@ -530,18 +552,11 @@ def run_msd(job, args, stream, peaks):
     autotuner candidate (the fastest is the autotuned b), with the rooflines of the
     stated and autotuned configurations and the per-epoch error against the FP64
     oracle on the 1% user subsample (stored traces; b = 128 and b = 32)."""
-    import shutil
     import torch
     import paper_2110_14044_gb300 as ials
     from paper_2110_14044_gb300 import _abi, autotune, synth
-    proc, out_dir = job
-    proc.join()
-    if proc.exitcode != 0:
-        return {"error": f"generator process exited with {proc.exitcode}"}
-    arrs = {k: np.load(os.path.join(out_dir, k + ".npy")) for k in ("u_indptr", "u_items", "i_indptr", "i_users")}
-    shutil.rmtree(out_dir, ignore_errors=True)
+    data = collect_generation(job)
     c = synth.PRESETS[MSD]
-    data = synth.Interactions(c["n_users"], c["n_items"], **arrs)
     d = c["d"]
     rows_plain = data.n_users + data.n_items
     out = {"workload": WORKLOADS[MSD], "initial_factors": "the library's seeded N(0, (0.1/sqrt(d))^2) draw",
@@ -594,27 +609,86 @@ def run_msd(job, args, stream, peaks):
     return out
 
 
-def run_convergence(prob, epochs):
+def run_convergence(prob, epochs, stream):
     """Objective (Eq. 2, FP64) after each of `epochs` epochs for every admissible
     block size, in both precisions, from the same initial factors (the analogue,
-    on the training objective, of the paper's quality-vs-b study)."""
+    on the training objective, of the paper's quality-vs-b study, Section 5.2.2),
+    with the device time of each epoch: b = 1 is iCD (Algorithm 2), b = d is iALS
+    (Algorithm 1), so the table is also the three-way runtime comparison at this d."""
+    import torch
     import paper_2110_14044_gb300 as ials
     from paper_2110_14044_gb300 import _abi, autotune
-    out = {"epochs": epochs, "desc": "objective after each epoch; same W0, H0 for every run"}
+    out = {"epochs": epochs, "d": prob.d,
+           "desc": "objective before and after each epoch and epoch seconds (graph replay; the "
+                   "first epoch includes the capture); same W0, H0 for every run"}
     for name, prec in (("fp32", _abi.PREC_FP32), ("bf16", _abi.PREC_BF16)):
         res = {}
         for b in autotune.CANDIDATES:
             if not autotune.admissible(prob.d, b, prec):
                 continue
             m = ials.Model(prob.data, prob.d, b, prob.alpha0, prob.lam, prob.nu, precision=prec,
-                           graph=True, W0=prob.W0, H0=prob.H0)
-            objs = [m.objective()]
+                           graph=True, W0=prob.W0, H0=prob.H0, stream=stream)
+            objs, secs = [m.objective()], []
             for _ in range(epochs):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
                 m.epoch(1)
+                e1.record(stream)
                 objs.append(m.objective())
-            res[str(b)] = objs
+                secs.append(e0.elapsed_time(e1) / 1e3)
+            res[str(b)] = {"objective": objs, "epoch_s": secs,
+                           "epoch_s_median_after_first": float(np.median(secs[1:])) if len(secs) > 1 else secs[0]}
             m.close()
         out[name] = res
+    return out
+
+
+# ------------------------------------------------------- the skewed-activity d sweep
+SWEEP = "skewed_136k"
+SWEEP_DIMS = (64, 256, 512, 2048)
+SWEEP_BLOCKS = (1, 8, 16, 32, 64, 128, 256)   # b = 1 (iCD) timed where d <= 256
+SWEEP_SPLITS = (512, 8192)                    # split lengths tried at the fastest b (0 = library's)
+
+
+def run_sweep(job, stream):
+    """Block size and work decomposition autotuned per d on the skewed-activity shape
+    (Zipf(1.3) users): d in {64, 256, 512, 2048}, FP32 and BF16 side by side, every
+    admissible b timed (one graph-replayed epoch after a warm-up epoch that captures
+    the graph), then the split length tuned at the fastest b.  Where b = 1 and b = d
+    are admissible the table holds the three-way comparison iCD / iALS++ / iALS."""
+    from paper_2110_14044_gb300 import _abi, autotune, synth
+    data = collect_generation(job)
+    c = synth.PRESETS[SWEEP]
+    lens = np.diff(data.u_indptr)
+    out = {"workload": WORKLOADS[SWEEP].replace("d=128, b=32, ", ""),
+           "max_user_row": int(lens.max()), "max_item_row": int(np.diff(data.i_indptr).max()),
+           "users_over_1000": int((lens > 1000).sum()),
+           "initial_factors": "the library's seeded N(0, (0.1/sqrt(d))^2) draw",
+           "timing": "1 epoch (graph replay) after 1 warm-up epoch, CUDA events", "dims": {}}
+    rows = data.n_users + data.n_items
+    for d in SWEEP_DIMS:
+        rec = {}
+        for pname, prec in (("fp32", _abi.PREC_FP32), ("bf16", _abi.PREC_BF16)):
+            by_b = {}
+            for b in SWEEP_BLOCKS:
+                if not autotune.admissible(d, b, prec) or (b == 1 and d > 256):
+                    continue
+                by_b[b] = autotune.time_epoch(data, d, b, c["alpha0"], c["lam"], c["nu"], prec,
+                                              epochs=1, stream=stream)
+            best = min(by_b, key=by_b.get)
+            by_split = {0: by_b[best]}
+            for sl in SWEEP_SPLITS:
+                by_split[sl] = autotune.time_epoch(data, d, best, c["alpha0"], c["lam"], c["nu"], prec,
+                                                   epochs=1, split_len=sl, stream=stream)
+            best_sl = min(by_split, key=by_split.get)
+            rec[pname] = {"epoch_s_by_b": {str(k): v for k, v in by_b.items()},
+                          "epoch_s_by_split_len": {str(k): v for k, v in by_split.items()},
+                          "autotuned": {"b": best, "split_len": best_sl, "epoch_s": by_split[best_sl],
+                                        "rows_per_s": rows * (d // best) / by_split[best_sl]}}
+        f = rec["fp32"]["epoch_s_by_b"]
+        rec["three_way_fp32"] = {"icd_b1_s": f.get("1"), "ialspp_s": rec["fp32"]["autotuned"]["epoch_s"],
+                                 "ialspp_b": rec["fp32"]["autotuned"]["b"], "ials_bd_s": f.get(str(d))}
+        out["dims"][str(d)] = rec
     return out
 
 
@@ -810,8 +884,11 @@ def main():
                     help="do not run the fold-in serving measurement")
     ap.add_argument("--autotune", action="store_true",
                     help="also time every admissible block size per precision (b sweep)")
-    ap.add_argument("--convergence", type=int, default=0, metavar="E",
-                    help="also record the objective over E epochs for every admissible b")
+    ap.add_argument("--convergence", type=int, default=None, metavar="E",
+                    help="record the objective over E epochs for every admissible b (0: skip; "
+                         "default 6 on the default workload, else 0)")
+    ap.add_argument("--no-sweep", dest="sweep", action="store_false",
+                    help="do not run the skewed-activity d x b sweep")
     ap.add_argument("--no-d1024", dest="d1024", action="store_false",
                     help="do not also measure the MSD-shaped d = 1024 workload")
     ap.add_argument("--d1024-steps", type=int, default=3,

@@ -84,6 +84,12 @@ typedef struct {
     uint64_t seed;
     int32_t precision;  /* IALS_PREC_* */
     int32_t flags;      /* IALS_FLAG_* */
+    int32_t split_len;  /* work decomposition: a row with more interactions than this is cut
+                         * into chunks (about equal, multiples of 32) whose statistics are
+                         * summed in chunk order; 0 = the library's choice from nnz
+                         * (clamp(nnz / 4864, 256, 8192)); else 32 <= split_len <= 2^24.
+                         * Ignored by ials_foldin_open. */
+    int32_t reserved;   /* must be 0 */
 } ials_params;
 
 /* Create a training context (Section 2 problem setting, Algorithm 3 state).

@@ -35,12 +35,12 @@ class Model:
 
     def __init__(self, data, d, b, alpha0, lam, nu=0.0, init_std=None, seed=0,
                  precision=_abi.PREC_FP32, graph=False, force_fp64=False, y=None, alpha=None,
-                 stream=None, W0=None, H0=None, general=False):
+                 stream=None, W0=None, H0=None, general=False, split_len=0):
         flags = ((_abi.FLAG_GRAPH if graph else 0) | (_abi.FLAG_FORCE_FP64 if force_fp64 else 0)
                  | (_abi.FLAG_GENERAL if general else 0))
         if init_std is None:
             init_std = 0.1 / np.sqrt(d)
-        self.params = make_params(d, b, alpha0, lam, nu, init_std, seed, precision, flags)
+        self.params = make_params(d, b, alpha0, lam, nu, init_std, seed, precision, flags, split_len)
         self.n_users, self.n_items, self.d, self.b = data.n_users, data.n_items, d, b
         self.nnz = int(data.u_indptr[-1])
         keep = lambda a, dt: None if a is None else np.ascontiguousarray(a, dtype=dt)

@@ -51,7 +51,8 @@ class ials_foldin_info(C.Structure):
 class ials_params(C.Structure):
     _fields_ = [("d", C.c_int32), ("b", C.c_int32), ("alpha0", C.c_double),
                 ("lambda_", C.c_double), ("nu", C.c_double), ("init_std", C.c_double),
-                ("seed", C.c_uint64), ("precision", C.c_int32), ("flags", C.c_int32)]
+                ("seed", C.c_uint64), ("precision", C.c_int32), ("flags", C.c_int32),
+                ("split_len", C.c_int32), ("reserved", C.c_int32)]
 
 
 _lib = None
@@ -122,9 +123,10 @@ def _stream(stream):
     return int(stream)
 
 
-def make_params(d, b, alpha0, lam, nu=0.0, init_std=0.01, seed=0, precision=PREC_FP32, flags=0):
+def make_params(d, b, alpha0, lam, nu=0.0, init_std=0.01, seed=0, precision=PREC_FP32, flags=0,
+                split_len=0):
     return ials_params(int(d), int(b), float(alpha0), float(lam), float(nu), float(init_std),
-                       int(seed), int(precision), int(flags))
+                       int(seed), int(precision), int(flags), int(split_len), 0)
 
 
 def ials_create(params, n_users, n_items, u_indptr, u_items, i_indptr=None, i_users=None,

@@ -525,6 +525,9 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
         return fail(IALS_EINVAL, "unknown precision");
     if (p.precision == IALS_PREC_BF16 && ((p.b != 16 && p.b != 32 && p.b != 64 && p.b != 128) || p.d % 8 != 0))
         return fail(IALS_EINVAL, "BF16 precision needs b in {16, 32, 64, 128} and d % 8 == 0");
+    if (p.split_len != 0 && (p.split_len < 32 || p.split_len > (1 << 24)))
+        return fail(IALS_EINVAL, "split_len must be 0 or in [32, 2^24]");
+    if (p.reserved != 0) return fail(IALS_EINVAL, "reserved must be 0");
     if (n_users <= 0 || n_items <= 0) return fail(IALS_EINVAL, "n_users and n_items must be > 0");
     if (nnz < 0 || nnz >= (int64_t)1 << 31) return fail(IALS_EINVAL, "nnz must be in [0, 2^31)");
     if (!u_indptr || (nnz > 0 && !u_items)) return fail(IALS_EINVAL, "user CSR missing");
@@ -614,7 +617,8 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     }
 
     // ---- work decomposition
-    const int64_t split_len = std::max<int64_t>(256, std::min<int64_t>(8192, nnz / (152 * 16 * 2)));
+    const int64_t split_len = p.split_len > 0 ? (int64_t)p.split_len
+                                              : std::max<int64_t>(256, std::min<int64_t>(8192, nnz / (152 * 16 * 2)));
     HostTasks ht[2] = {build_tasks(uptr, n_users, split_len), build_tasks(iptr, n_items, split_len)};
     for (int sd = 0; sd < 2; ++sd)
         for (const Task &t : ht[sd].tasks) {

@@ -46,7 +46,7 @@ def test_binding_covers_every_declared_symbol():
 
 def test_params_struct_layout():
     # d, b, alpha0, lambda, nu, init_std, seed, precision, flags (C layout with padding)
-    assert ctypes.sizeof(_abi.ials_params) == 4 + 4 + 8 * 4 + 8 + 4 + 4
+    assert ctypes.sizeof(_abi.ials_params) == 4 + 4 + 8 * 4 + 8 + 4 + 4 + 4 + 4
 
 
 def test_last_error_is_callable_without_gpu(lib):
@@ -69,7 +69,8 @@ def _create(p, n_users, n_items, uptr, uidx, **kw):
 
 @pytest.mark.parametrize("case", ["d", "b_not_dividing", "bf16_b", "alpha0",
                                   "indptr_end", "indptr_order", "item_range", "repeat",
-                                  "transpose_len", "transpose_pairs", "alpha_zero", "y_nan"])
+                                  "transpose_len", "transpose_pairs", "alpha_zero", "y_nan",
+                                  "split_len_small", "split_len_large", "reserved"])
 def test_create_validates_on_the_host(case):
     """Every argument check runs on the host before any device work, so a bad
     input is rejected with IALS_EINVAL and a message, GPU or not."""
@@ -105,6 +106,13 @@ def test_create_validates_on_the_host(case):
         kw["alpha"] = np.array([1, 1, 0, 1, 1], np.float32)
     elif case == "y_nan":
         kw["y"] = np.array([1, np.nan, 1, 1, 1], np.float32)
+    elif case == "split_len_small":
+        good["p"] = _abi.make_params(16, 8, 0.1, 0.01, split_len=31)
+    elif case == "split_len_large":
+        good["p"] = _abi.make_params(16, 8, 0.1, 0.01, split_len=(1 << 24) + 1)
+    elif case == "reserved":
+        good["p"] = _abi.make_params(16, 8, 0.1, 0.01)
+        good["p"].reserved = 1
     with pytest.raises(_abi.IalsError) as ei:
         _create(**good, **kw)
     assert ei.value.status == _abi.EINVAL, (case, str(ei.value))

@@ -454,6 +454,38 @@ def test_autotuner_returns_the_fastest_admissible_block():
     assert set(t16) == {16, 32, 64}
 
 
+def test_autotuner_tunes_the_split_length_at_the_chosen_block():
+    from paper_2110_14044_gb300 import autotune
+    prob = synth.preset("skewed_136k", seed=61, n_users=3000, n_items=600, nnz=90_000, d=64)
+    res = autotune.autotune(prob.data, 64, 0.1, 1e-3, 1.0, candidates=(16, 32),
+                            split_candidates=(0, 64, 256), epochs=1, W0=prob.W0, H0=prob.H0)
+    assert res["b"] in (16, 32) and res["b"] == min(res["epoch_s_by_b"], key=res["epoch_s_by_b"].get)
+    assert set(res["epoch_s_by_split_len"]) == {0, 64, 256}
+    assert res["split_len"] == min(res["epoch_s_by_split_len"], key=res["epoch_s_by_split_len"].get)
+    assert res["epoch_s"] == res["epoch_s_by_split_len"][res["split_len"]]
+
+
+@pytest.mark.parametrize("split_len,precision", [(32, _abi.PREC_FP32), (96, _abi.PREC_FP32),
+                                                 (64, _abi.PREC_BF16)])
+def test_short_split_length_matches_oracle(split_len, precision):
+    """A split length far below the default cuts most rows into many chunks (and
+    the longest into hundreds): the chunk-order sums still give the oracle's epoch."""
+    d, b = 64, 32
+    prob = synth.preset("skewed_136k", seed=62, n_users=2000, n_items=500, nnz=60_000, d=d)
+    data = prob.data
+    m = Model(data, d, b, 0.1, 1e-3, 1.0, precision=precision, W0=prob.W0, H0=prob.H0,
+              split_len=split_len)
+    P = oracle.Problem.from_data(data, d, b, 0.1, 1e-3, 1.0)
+    Wr, Hr, _, _, _ = oracle.ialspp(P, 2, prob.W0, prob.H0)
+    o, st = m.epoch(2, objective=True)
+    assert st == 0
+    ref = oracle.objective(P, Wr, Hr)
+    W, H = m.factors()
+    tol_obj, tol_emb = (OBJ_TOL, EMB_TOL) if precision == _abi.PREC_FP32 else (1e-3, 5e-2)
+    assert abs(o - ref) / ref <= tol_obj
+    assert rel_embed_err(W, Wr) <= tol_emb and rel_embed_err(H, Hr) <= tol_emb
+
+
 @pytest.mark.parametrize("b,precision", [(16, _abi.PREC_FP32), (64, _abi.PREC_FP32), (32, _abi.PREC_BF16)])
 def test_skewed_user_activity_epochs(b, precision):
     """Zipf(1.3) user activity with rows capped at the whole catalogue (the skewed
