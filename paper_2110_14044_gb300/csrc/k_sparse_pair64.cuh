@@ -49,11 +49,24 @@ struct Pair64 {
     static_assert(B * B <= NS * STAGE, "the system fits in the staging buffers");
 };
 
-struct Pair64Smem {
+// BF16 statistics: a stage holds the hi and lo tiles of a chunk (bf16, rows of
+// 72 with the residual in column 64).
+struct Pair64Bf {
+    static constexpr int B = 64, PAIRS = 4, THREADS = 64 * PAIRS;
+    static constexpr int CH = 32, SBH = CtaBfCfg<64>::SBH, TILE = CH * SBH, STAGE = TILE;  // floats = 2 TILE bf16
+    static constexpr int P = 1, NS = P + 1, NI = 2 * P + 1;
+    static constexpr int GJB = Pair64::GJB;
+    static constexpr int FLOATS = NS * STAGE + 2 * NS * CH + 2 * NI * CH + GJB + B + 4;
+    static constexpr int SMEM_BYTES = PAIRS * FLOATS * 4;
+    static_assert(FLOATS % 4 == 0, "pair regions stay 16-byte aligned");
+    static_assert(B * B <= NS * STAGE, "the system fits in the staging buffers");
+};
+
+template <class C>
+struct PairSmem {
     float *stage, *she, *sha, *gjb, *dl;  // gjb: Gauss-Jordan exchange; dl: right-hand side, then solution
     int *ci, *cq, *flag;                  // flag[0]: next task
-    __device__ __forceinline__ explicit Pair64Smem(float *base) {
-        using C = Pair64;
+    __device__ __forceinline__ explicit PairSmem(float *base) {
         stage = base;
         she = stage + C::NS * C::STAGE;
         sha = she + C::NS * C::CH;
@@ -64,6 +77,7 @@ struct Pair64Smem {
         flag = reinterpret_cast<int *>(dl + C::B);
     }
 };
+using Pair64Smem = PairSmem<Pair64>;
 
 // The 4 x 8 half tile of pair thread u: rows 8 ti + 4 h .. + 3, columns 8 tj .. + 7.
 // u < 56: off-diagonal tile u / 2 (ti > tj, in row-major lower order), half u % 2;
@@ -136,12 +150,12 @@ __device__ __forceinline__ int p64_at(int r, int half, int group) {
 // (double-buffered exchange).  Pivots are checked against the original diagonal
 // (not below 1e-5 of it, finite).  Returns 0 (uniformly) when every pivot passed
 // and the solution is finite; x[t] is then solution entry 2 q + t.
-__device__ __forceinline__ int p64_gj(float (&A)[2][32], float (&g)[2], float dorig, const Pair64Smem &S, int pr,
-                                      int pt, bool force_fail, float (&x)[2]) {
+__device__ __forceinline__ int p64_gj(float (&A)[2][32], float (&g)[2], float dorig, float *gjb, int pr, int pt,
+                                      bool force_fail, float (&x)[2]) {
     const int rq = pt >> 1, ch = pt & 1, hw = pt >> 5;
-    float *pub = S.gjb;                    // [2 steps][2 columns][2 (row % 2)][36: row / 2, padding]
-    float *gb = S.gjb + 288;               // [2 steps][2]
-    int *vote = reinterpret_cast<int *>(S.gjb + 292);
+    float *pub = gjb;                      // [2 steps][2 columns][2 (row % 2)][36: row / 2, padding]
+    float *gb = gjb + 288;                 // [2 steps][2]
+    int *vote = reinterpret_cast<int *>(gjb + 292);
     bool bad = force_fail;
     float pa = 1.f, pb = 0.f, pc = 1.f;
 #pragma unroll
@@ -382,7 +396,7 @@ __global__ void __launch_bounds__(Pair64::THREADS, 2) k_sparse_pair64(const Step
         }
         const int rown = 2 * rq + chh;  // the row whose diagonal entry this thread holds
         const float dorig = M[p64_at(rown, chh, rq >> 2) + (rq & 3)];
-        const int vote = p64_gj(A, gr, dorig, S, pr, pt, a.force_fp64 != 0, x);
+        const int vote = p64_gj(A, gr, dorig, S.gjb, pr, pt, a.force_fp64 != 0, x);
         if (vote) {
             if (pt == 0) {
                 const int i = atomicAdd(a.retry, 1);
@@ -402,11 +416,12 @@ __global__ void __launch_bounds__(Pair64::THREADS, 2) k_sparse_pair64(const Step
         auto rbody = [&](int j, int sb, int ib) {
             const int cnt = cnt_of(j);
             float t = 0.f;
-            if (k < cnt) {  // float4 groups 2 u + part: the two threads' loads fall in different banks
-                const float *xk = S.stage + sb * C::STAGE + k * SB + 4 * part;
-                const float *dv = S.dl + 4 * part;
+            if (k < cnt) {  // float4 groups 0-3, 8-11 (part 0) and 4-7, 12-15 (part 1): no bank conflicts
+                const float *xk = S.stage + sb * C::STAGE + k * SB + 16 * part;
+                const float *dv = S.dl + 16 * part;
 #pragma unroll
-                for (int m = 0; m < 64; m += 8) {
+                for (int u = 0; u < 8; ++u) {
+                    const int m = 4 * (u & 3) + 32 * (u >> 2);
                     const float4 f = p64_ld4(xk + m), w = p64_ld4(dv + m);
                     t = fmaf(w.x, f.x, t);
                     t = fmaf(w.y, f.y, t);
@@ -470,6 +485,340 @@ cudaError_t launch_sparse_pair64_all(const StepArgs &a, cudaStream_t s) {
     }
     {  // always called: the first call sizes the grid, outside any stream capture
         const cudaError_t e = launch_split_resid_reg<64, PERM>(a, s);
+        if (e != cudaSuccess) return e;
+    }
+    prof_mark(a.prof, K_RETRY, s);
+    k_retry_cta<64, PERM, HAS_A, false><<<kRetryBlocks, CF::THREADS, retry_cta_smem<64>(), s>>>(a);
+    prof_mark(a.prof, -1, s);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ BF16 statistics
+
+// Entry (r, c) of the solve layout of p64_gj.
+__device__ __forceinline__ float *p64_entry(float *M, int r, int c) {
+    const int m = c >> 1;
+    return M + p64_at(r, c & 1, m >> 2) + (m & 3);
+}
+
+// Pair warp PW does the tile lists of the CTA kernel's warps 2 PW and 2 PW + 1
+// (k_sparse_cta_bf16.cuh): two 16-row blocks of the lower triangle, both halves,
+// and their gradient tiles, as compensated hi/lo mma.sync products; the
+// fragments of the blocks the two lists share are loaded once.
+template <int PW>
+__device__ __forceinline__ void pbf_kstep(float (&acc)[2][5][4], float (&gac)[2][4], const __nv_bfloat16 *th,
+                                          const __nv_bfloat16 *tl, int ks, int lane) {
+    using W0 = CtaBfWarp<64, 2 * PW>;
+    using W1 = CtaBfWarp<64, 2 * PW + 1>;
+    constexpr int MT = 4, SBH = CtaBfCfg<64>::SBH, NPT = CtaBfCfg<64>::NPT;
+    constexpr unsigned MASK = W0::blocks() | W1::blocks();
+    const int mj = lane >> 3, mr = lane & 7;
+    unsigned Rh[MT][4], Rl[MT][4], E[4];
+#pragma unroll
+    for (int g = 0; g < MT; ++g) {
+        if ((MASK >> g) & 1u) {
+            const int off = (ks * 16 + (mj >> 1) * 8 + mr) * SBH + g * 16 + (mj & 1) * 8;
+            ldsm_x4_t(Rh[g], th + off);
+            ldsm_x4_t(Rl[g], tl + off);
+        }
+    }
+    ldsm_x4_t(E, (mj < 2 ? th : tl) + (ks * 16 + (mj & 1) * 8 + mr) * SBH + 64);
+#pragma unroll
+    for (int s = 0; s < NPT; ++s) {
+        {
+            const int i = W0::ti(s), n = W0::tn(s), g2 = n >> 1, h = n & 1;
+            mma_bf16(acc[0][s], Rh[i], Rh[g2][h], Rh[g2][h + 2]);
+            mma_bf16(acc[0][s], Rh[i], Rl[g2][h], Rl[g2][h + 2]);
+            mma_bf16(acc[0][s], Rl[i], Rh[g2][h], Rh[g2][h + 2]);
+        }
+        {
+            const int i = W1::ti(s), n = W1::tn(s), g2 = n >> 1, h = n & 1;
+            mma_bf16(acc[1][s], Rh[i], Rh[g2][h], Rh[g2][h + 2]);
+            mma_bf16(acc[1][s], Rh[i], Rl[g2][h], Rl[g2][h + 2]);
+            mma_bf16(acc[1][s], Rl[i], Rh[g2][h], Rh[g2][h + 2]);
+        }
+    }
+    mma_bf16(gac[0], Rh[W0::GRAD], E[0], E[1]);
+    mma_bf16(gac[0], Rh[W0::GRAD], E[2], E[3]);
+    mma_bf16(gac[0], Rl[W0::GRAD], E[0], E[1]);
+    mma_bf16(gac[1], Rh[W1::GRAD], E[0], E[1]);
+    mma_bf16(gac[1], Rh[W1::GRAD], E[2], E[3]);
+    mma_bf16(gac[1], Rl[W1::GRAD], E[0], E[1]);
+}
+
+// Tile list W's accumulators into the solve layout (entries on or below the
+// diagonal, mirrored, so the system is exactly symmetric) or, for a chunk of a
+// long row, into its slot (lower 8 x 8 tiles, diagonal tiles mirrored); the
+// gradient into rhs (length 64).
+template <int W, bool SLOT>
+__device__ __forceinline__ void pbf_store(const float (&acc)[5][4], const float (&gac)[4], float *M, float *rhs,
+                                          int lane) {
+    using WT = CtaBfWarp<64, W>;
+    const int r = lane >> 2, c2 = 2 * (lane & 3);
+#pragma unroll
+    for (int s = 0; s < CtaBfCfg<64>::NPT; ++s) {
+        const int i = WT::ti(s), n = WT::tn(s);
+#pragma unroll
+        for (int hr = 0; hr < 2; ++hr)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int rr = 16 * i + r + 8 * hr, cc = 8 * n + c2 + e;
+                const float v = acc[s][2 * hr + e];
+                if (cc <= rr) {
+                    if (SLOT) {
+                        M[rr * 64 + cc] = v;
+                        if (cc < rr && (cc >> 3) == (rr >> 3)) M[cc * 64 + rr] = v;
+                    } else {
+                        *p64_entry(M, rr, cc) = v;
+                        if (cc < rr) *p64_entry(M, cc, rr) = v;
+                    }
+                }
+            }
+    }
+    if ((lane & 3) == 0) {
+        rhs[16 * WT::GRAD + r] = gac[0];
+        rhs[16 * WT::GRAD + r + 8] = gac[2];
+    }
+}
+
+template <bool PERM, bool HAS_A>
+__global__ void __launch_bounds__(Pair64Bf::THREADS, 2) k_sparse_pair64_bf16(const StepArgs a) {
+    using C = Pair64Bf;
+    constexpr int B = 64, CH = C::CH, SBH = C::SBH, NPT = CtaBfCfg<64>::NPT;
+    extern __shared__ float4 smem4[];
+    const int pr = threadIdx.x >> 6, pt = threadIdx.x & 63, pw = pt >> 5, lane = pt & 31;
+    const PairSmem<C> S(reinterpret_cast<float *>(smem4) + pr * C::FLOATS);
+    if (pt == 0) S.flag[0] = atomicAdd(a.counter, 1);
+    for (;;) {
+        pair_sync(pr);
+        const int tsk = S.flag[0];
+        if (tsk >= a.n_tasks) break;
+        pair_sync(pr);
+        if (pt == 0) S.flag[0] = atomicAdd(a.counter, 1);
+        const Task tk = a.tasks[tsk];
+        const int nch = (tk.len + CH - 1) / CH;
+        float acc[2][NPT][4], gac[2][4];
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+#pragma unroll
+            for (int t = 0; t < NPT; ++t)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[l][t][q] = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) gac[l][q] = 0.f;
+        }
+        if (tk.slot < 0) {  // alpha0 G_pipi + lambda_r I and the row term
+            const float lam = a.lambda * (1.0f + a.nu * (float)tk.len);
+            if (pw == 0) {
+                cta_bf_init<64, 0>(acc[0], gac[0], a, tk.row, lam, lane);
+                cta_bf_init<64, 1>(acc[1], gac[1], a, tk.row, lam, lane);
+            } else {
+                cta_bf_init<64, 2>(acc[0], gac[0], a, tk.row, lam, lane);
+                cta_bf_init<64, 3>(acc[1], gac[1], a, tk.row, lam, lane);
+            }
+        }
+        auto cnt_of = [&](int c) { return min(CH, tk.len - c * CH); };
+        auto stage0 = [&](int i, int ib) {
+            const int cnt = cnt_of(i);
+            const int64_t s0 = tk.begin + (int64_t)i * CH;
+            if (pt < cnt) cp_async4(S.ci + ib * CH + pt, a.idx + s0 + pt);
+            if (PERM && pt >= 32 && pt - 32 < cnt) cp_async4(S.cq + ib * CH + pt - 32, a.pos + s0 + pt - 32);
+        };
+        auto gather = [&](int i, int sb, int ib) {  // hi and lo slices of chunk i
+            const int cnt = cnt_of(i);
+            const int *ids = S.ci + ib * CH;
+            __nv_bfloat16 *th = reinterpret_cast<__nv_bfloat16 *>(S.stage + sb * C::STAGE), *tl = th + C::TILE;
+            for (int f = pt; f < cnt * 16; f += 64) {
+                const int k = f >> 4, v = f & 15, half = v >> 3, vc = v & 7;
+                cp_async16((half ? tl : th) + k * SBH + vc * 8,
+                           (half ? a.Fl : a.Fh) + (int64_t)ids[k] * a.d + a.p0 + vc * 8);
+            }
+        };
+        auto stage1 = [&](int i, int sb, int ib) {
+            const int cnt = cnt_of(i);
+            __nv_bfloat16 *th = reinterpret_cast<__nv_bfloat16 *>(S.stage + sb * C::STAGE), *tl = th + C::TILE;
+            const int rows16 = (cnt + 15) & ~15;  // rows cnt .. rows16 - 1 take part in the k-steps: zero
+            for (int rr = cnt + pt; rr < rows16; rr += 64) {
+#pragma unroll
+                for (int v = 0; v < SBH / 8; ++v) {
+                    reinterpret_cast<uint4 *>(th + rr * SBH)[v] = make_uint4(0u, 0u, 0u, 0u);
+                    reinterpret_cast<uint4 *>(tl + rr * SBH)[v] = make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
+            gather(i, sb, ib);
+            if (pt < cnt) {
+                const int64_t q = PERM ? (int64_t)S.cq[ib * CH + pt] : tk.begin + (int64_t)i * CH + pt;
+                cp_async4(S.she + sb * CH + pt, a.e + q);
+                if (HAS_A) cp_async4(S.sha + sb * CH + pt, a.alpha + q);
+            }
+        };
+        auto body = [&](int j, int sb, int) {
+            const int cnt = cnt_of(j);
+            __nv_bfloat16 *th = reinterpret_cast<__nv_bfloat16 *>(S.stage + sb * C::STAGE), *tl = th + C::TILE;
+            if (HAS_A) {  // weighted: row and residual times sqrt(alpha), split into hi / lo again
+                const int k = pt >> 1, hf = pt & 1;
+                if (k < cnt) {
+                    const float sa = sqrtf(S.sha[sb * CH + k]);
+#pragma unroll
+                    for (int v = 4 * hf; v < 4 * hf + 4; ++v) {
+                        uint4 hv = reinterpret_cast<uint4 *>(th + k * SBH)[v];
+                        uint4 lv = reinterpret_cast<uint4 *>(tl + k * SBH)[v];
+                        __nv_bfloat162 *h2 = reinterpret_cast<__nv_bfloat162 *>(&hv);
+                        __nv_bfloat162 *l2 = reinterpret_cast<__nv_bfloat162 *>(&lv);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float2 hf2 = __bfloat1622float2(h2[q]), lf2 = __bfloat1622float2(l2[q]);
+                            const float x0 = (hf2.x + lf2.x) * sa, x1 = (hf2.y + lf2.y) * sa;
+                            const __nv_bfloat162 nh = __floats2bfloat162_rn(x0, x1);
+                            const float2 nhf = __bfloat1622float2(nh);
+                            h2[q] = nh;
+                            l2[q] = __floats2bfloat162_rn(x0 - nhf.x, x1 - nhf.y);
+                        }
+                        reinterpret_cast<uint4 *>(th + k * SBH)[v] = hv;
+                        reinterpret_cast<uint4 *>(tl + k * SBH)[v] = lv;
+                    }
+                    if (hf == 0) {
+                        const float e = S.she[sb * CH + k] * sa;
+                        const __nv_bfloat16 h = __float2bfloat16_rn(e);
+                        th[k * SBH + B] = h;
+                        tl[k * SBH + B] = __float2bfloat16_rn(e - __bfloat162float(h));
+                    }
+                }
+            } else if (pt < cnt) {  // the residual column, hi / lo
+                const float e = S.she[sb * CH + pt];
+                const __nv_bfloat16 h = __float2bfloat16_rn(e);
+                th[pt * SBH + B] = h;
+                tl[pt * SBH + B] = __float2bfloat16_rn(e - __bfloat162float(h));
+            }
+            pair_sync(pr);
+            const int ksteps = (cnt + 15) >> 4;
+            for (int ks = 0; ks < ksteps; ++ks) {
+                if (pw == 0) pbf_kstep<0>(acc, gac, th, tl, ks, lane);
+                else pbf_kstep<1>(acc, gac, th, tl, ks, lane);
+            }
+        };
+        p64_pipeline(pr, nch, stage0, stage1, body);
+        if (tk.slot >= 0) {  // chunk of a long row: its statistics to the slot
+            float *Pp = a.part + (int64_t)tk.slot * (B * B + B);
+            if (pw == 0) {
+                pbf_store<0, true>(acc[0], gac[0], Pp, Pp + B * B, lane);
+                pbf_store<1, true>(acc[1], gac[1], Pp, Pp + B * B, lane);
+            } else {
+                pbf_store<2, true>(acc[0], gac[0], Pp, Pp + B * B, lane);
+                pbf_store<3, true>(acc[1], gac[1], Pp, Pp + B * B, lane);
+            }
+            continue;
+        }
+        float *M = S.stage;
+        if (pw == 0) {
+            pbf_store<0, false>(acc[0], gac[0], M, S.dl, lane);
+            pbf_store<1, false>(acc[1], gac[1], M, S.dl, lane);
+        } else {
+            pbf_store<2, false>(acc[0], gac[0], M, S.dl, lane);
+            pbf_store<3, false>(acc[1], gac[1], M, S.dl, lane);
+        }
+        pair_sync(pr);
+        const int rq = pt >> 1, chh = pt & 1;
+        float A[2][32], gr[2], x[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int r = 2 * rq + t;
+#pragma unroll
+            for (int q4 = 0; q4 < 8; ++q4) {
+                const float4 u = p64_ld4(M + p64_at(r, chh, q4));
+                A[t][4 * q4] = u.x; A[t][4 * q4 + 1] = u.y; A[t][4 * q4 + 2] = u.z; A[t][4 * q4 + 3] = u.w;
+            }
+            gr[t] = S.dl[r];
+        }
+        const float dorig = *p64_entry(M, 2 * rq + chh, 2 * rq + chh);
+        const int vote = p64_gj(A, gr, dorig, S.gjb, pr, pt, a.force_fp64 != 0, x);
+        if (vote) {
+            if (pt == 0) {
+                const int i = atomicAdd(a.retry, 1);
+                a.retry[1 + i] = tk.row;
+            }
+            continue;
+        }
+        if (chh == 0) {
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                apply_delta(a.X, a.Xh, a.Xl, (int64_t)tk.row * a.d + a.p0 + 2 * rq + t, x[t]);
+                S.dl[2 * rq + t] = x[t];
+            }
+        }
+        // residual update from the re-gathered hi + lo slices: two threads per
+        // interaction, 16-byte chunks u + 4 part of the row
+        const int k = pt >> 1, part = pt & 1;
+        auto rbody = [&](int j, int sb, int ib) {
+            const int cnt = cnt_of(j);
+            const __nv_bfloat16 *th = reinterpret_cast<const __nv_bfloat16 *>(S.stage + sb * C::STAGE);
+            const __nv_bfloat16 *tl = th + C::TILE;
+            float t = 0.f;
+            if (k < cnt) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int c8 = u + 4 * part;
+                    const uint4 hv = *reinterpret_cast<const uint4 *>(th + k * SBH + 8 * c8);
+                    const uint4 lv = *reinterpret_cast<const uint4 *>(tl + k * SBH + 8 * c8);
+                    const float4 w0 = p64_ld4(S.dl + 8 * c8), w1 = p64_ld4(S.dl + 8 * c8 + 4);
+                    const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                    const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&hv);
+                    const __nv_bfloat162 *l2 = reinterpret_cast<const __nv_bfloat162 *>(&lv);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float2 hf2 = __bfloat1622float2(h2[q]), lf2 = __bfloat1622float2(l2[q]);
+                        t = fmaf(w[2 * q], hf2.x + lf2.x, t);
+                        t = fmaf(w[2 * q + 1], hf2.y + lf2.y, t);
+                    }
+                }
+            }
+            t += __shfl_xor_sync(kFull, t, 1);
+            if (k < cnt && part == 0) {
+                const int64_t q = PERM ? (int64_t)S.cq[ib * CH + k] : tk.begin + (int64_t)j * CH + k;
+                a.e[q] -= t;
+            }
+        };
+        p64_pipeline(pr, nch, stage0, gather, rbody);
+    }
+}
+
+template <bool PERM, bool HAS_A>
+cudaError_t launch_sparse_pair64_bf16_all(const StepArgs &a, cudaStream_t s) {
+    using C = Pair64Bf;
+    using CF = CtaCfg<64>;
+    static bool attr_done = false;
+    static int per_sm = 0;
+    auto kern = k_sparse_pair64_bf16<PERM, HAS_A>;
+    if (!attr_done) {
+        cudaError_t e;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES)) != cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(k_split_solve_rc<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      RcCfg<64>::SMEM_BYTES)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_retry_cta<64, PERM, HAS_A, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, retry_cta_smem<64>())) != cudaSuccess)
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::THREADS, C::SMEM_BYTES)) != cudaSuccess)
+            return e;
+        if (per_sm < 1) per_sm = 1;
+        attr_done = true;
+    }
+    if (a.n_tasks > 0) {
+        int grid = 152 * per_sm;
+        const int need = (a.n_tasks + C::PAIRS - 1) / C::PAIRS;
+        if (grid > need) grid = need;
+        prof_mark(a.prof, K_SPARSE, s);
+        kern<<<grid, C::THREADS, C::SMEM_BYTES, s>>>(a);
+        prof_mark(a.prof, -1, s);
+    }
+    if (a.n_split > 0) {
+        const int g2 = a.n_split < 152 * 4 ? a.n_split : 152 * 4;
+        prof_mark(a.prof, K_SPLIT_SOLVE, s);
+        k_split_solve_rc<64, false><<<g2, RcCfg<64>::THREADS, RcCfg<64>::SMEM_BYTES, s>>>(a);
+        prof_mark(a.prof, -1, s);
+    }
+    {
+        const cudaError_t e = launch_split_resid_reg_bf16<64, PERM>(a, s);
         if (e != cudaSuccess) return e;
     }
     prof_mark(a.prof, K_RETRY, s);
