@@ -32,9 +32,25 @@
 // the split-row solve, as the other kernels do.
 #pragma once
 
-#include "k_sparse_gj64.cuh"
+#include "k_sparse_cta_bf16.cuh"
+#include "k_sparse_rc.cuh"
 
 namespace ials {
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// Barrier of the two warps (64 threads) of pair `pr` (ids 1 .. 4; id 0 is
+// __syncthreads).
+__device__ __forceinline__ void pair_sync(int pr) {
+    asm volatile("bar.sync %0, 64;\n" ::"r"(pr + 1) : "memory");
+}
 
 struct Pair64 {
     static constexpr int B = 64, PAIRS = 4, THREADS = 64 * PAIRS;
@@ -101,8 +117,12 @@ __device__ __forceinline__ void p64_st4(float *p, float x, float y, float z, flo
     *reinterpret_cast<float4 *>(p) = make_float4(x, y, z, w);
 }
 
-// Software pipeline of one pair over `total` chunks (see gj64_pipeline; the
-// barrier is the pair's own).
+// Software pipeline of one pair over `total` chunks.  stage0(i, ib): cp.async of
+// chunk i's column ids / positions into id stage ib; stage1(i, sb, ib): the
+// gathers of chunk i (reading its ids from id stage ib) into slice stage sb;
+// body(j, sb, ib): the work on chunk j.  Every iteration commits one cp.async
+// group, so waiting for all but the last P - 1 groups leaves chunk j's slices
+// (and chunk j + P's ids) complete; the pair's barrier then publishes them.
 template <typename S0, typename S1, typename Body>
 __device__ __forceinline__ void p64_pipeline(int pr, int total, S0 stage0, S1 stage1, Body body) {
     constexpr int P = Pair64::P, NS = Pair64::NS, NI = Pair64::NI;
