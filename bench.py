@@ -55,7 +55,7 @@ NCU_TRAFFIC = {
     ("sparse", "bf16"): {"workload": ("ml20m_136k", 128, 32),
                          "sources": ["paper_2110_14044_gb300/csrc/k_sparse_bf16.cuh",
                                      "paper_2110_14044_gb300/csrc/k_sparse_impl.cuh"],
-                         "sha256_16": "649ef0cd0d70fba4", "bytes_per_launch": 287.8e6},
+                         "sha256_16": "c21d3725b581eb54", "bytes_per_launch": 288.1e6},
     ("sparse", "fp32"): {"workload": ("ml20m_136k", 128, 32),
                          "sources": ["paper_2110_14044_gb300/csrc/k_sparse_impl.cuh"],
                          "sha256_16": "d5231016883d3cc7", "bytes_per_launch": 183.2e6},
@@ -698,7 +698,11 @@ def run_ncu_step(args):
     from paper_2110_14044_gb300 import _abi, build, synth
     build.build()
     import paper_2110_14044_gb300 as ials
-    prob = synth.preset(args.workload, seed=0, **overrides(args))
+    o = overrides(args)
+    if args.ncu_frac < 1.0:  # a user sample of the workload (same shapes otherwise), for short captures
+        c = synth.PRESETS[args.workload]
+        o.update(n_users=max(1, int(c["n_users"] * args.ncu_frac)), nnz=max(1, int(c["nnz"] * args.ncu_frac)))
+    prob = synth.preset(args.workload, seed=0, **o)
     prec = _abi.PREC_BF16 if args.precision == "bf16" else _abi.PREC_FP32
     m = ials.Model(prob.data, prob.d, prob.b, prob.alpha0, prob.lam, prob.nu, precision=prec,
                    W0=prob.W0, H0=prob.H0)
@@ -895,6 +899,8 @@ def main():
                     help="timed epochs per configuration of the d = 1024 workload")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-frac", type=float, default=1.0,
+                    help="with --ncu-step: use this fraction of the workload's users and positives")
     ap.add_argument("--ncu-step", action="store_true",
                     help="run one user and one item block step only (for profiler captures)")
     ap.add_argument("--ncu-foldin", action="store_true",

@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(256, 2) k_gram_big(const float *__restrict__ X
 }
 
 // Large-d row terms (d % 16 == 0, bs % 32 == 0): 256 rows x 32 block columns per
-// block, 256 threads with 8 rows x 4 columns each; X rows and G in 16-wide
+// block (a 1-D grid, column block fastest), 256 threads with 8 rows x 4 columns each; X rows and G in 16-wide
 // k-slabs staged by cp.async into two buffers (rows padded to 20 floats).
 constexpr int RB_TM = 256, RB_TN = 32, RB_KS = 16, RB_SA = RB_KS + 4;
 
@@ -404,8 +404,11 @@ __global__ void __launch_bounds__(256, 2) k_rowterm_big(const float *__restrict_
     __shared__ __align__(16) float As[2][RB_TM * RB_SA];
     __shared__ __align__(16) float Bs[2][RB_KS * RB_TN];
     const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
-    const int64_t r0 = (int64_t)blockIdx.x * RB_TM;
-    const int n0 = blockIdx.y * RB_TN;
+    // the column blocks of one row tile are consecutive blocks, so the tile's rows are
+    // read from DRAM once and then hit in L2
+    const int ncb = bs / RB_TN;
+    const int64_t r0 = (int64_t)(blockIdx.x / ncb) * RB_TM;
+    const int n0 = (int)(blockIdx.x % ncb) * RB_TN;
     float acc[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
@@ -813,7 +816,7 @@ cudaError_t launch_rowterm(const float *X, const int64_t *ptr, int32_t n_rows, i
                            float nu, float *R, cudaStream_t s) {
     if (n_rows == 0) return cudaSuccess;
     if (d % RB_KS == 0 && bs % RB_TN == 0) {
-        const dim3 grid((unsigned)((n_rows + RB_TM - 1) / RB_TM), bs / RB_TN);
+        const unsigned grid = (unsigned)(((int64_t)n_rows + RB_TM - 1) / RB_TM * (bs / RB_TN));
         k_rowterm_big<<<grid, 256, 0, s>>>(X, ptr, n_rows, d, p0, bs, G, alpha0, lambda, nu, R);
         return cudaGetLastError();
     }
