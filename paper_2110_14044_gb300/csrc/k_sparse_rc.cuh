@@ -1,4 +1,4 @@
-// Block step of Algorithm 3 for block sizes B = 64 and 128 with the b x b
+// Block step of Algorithm 3 for block sizes B = 64, 128 and 256 with the b x b
 // system of a row held in registers, spread over the CTA (one CTA per task).
 //
 // A_r is cut into 8 x 8 tiles; the NTL = NB (NB + 1) / 2 tiles on or below
