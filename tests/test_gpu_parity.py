@@ -465,12 +465,13 @@ def test_autotuner_tunes_the_split_length_at_the_chosen_block():
     assert res["epoch_s"] == res["epoch_s_by_split_len"][res["split_len"]]
 
 
-@pytest.mark.parametrize("split_len,precision", [(32, _abi.PREC_FP32), (96, _abi.PREC_FP32),
-                                                 (64, _abi.PREC_BF16)])
-def test_short_split_length_matches_oracle(split_len, precision):
+@pytest.mark.parametrize("split_len,precision,d,b", [(32, _abi.PREC_FP32, 64, 32), (96, _abi.PREC_FP32, 64, 32),
+                                                     (64, _abi.PREC_BF16, 64, 32), (64, _abi.PREC_FP32, 128, 64),
+                                                     (96, _abi.PREC_BF16, 128, 64)])
+def test_short_split_length_matches_oracle(split_len, precision, d, b):
     """A split length far below the default cuts most rows into many chunks (and
-    the longest into hundreds): the chunk-order sums still give the oracle's epoch."""
-    d, b = 64, 32
+    the longest into hundreds): the chunk-order sums still give the oracle's epoch
+    (b = 32: warp kernels; b = 64: the warp-pair kernels and their split-row solve)."""
     prob = synth.preset("skewed_136k", seed=62, n_users=2000, n_items=500, nnz=60_000, d=d)
     data = prob.data
     m = Model(data, d, b, 0.1, 1e-3, 1.0, precision=precision, W0=prob.W0, H0=prob.H0,
