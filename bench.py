@@ -677,7 +677,8 @@ def run_sweep(job, stream):
     (Zipf(1.3) users): d in {64, 256, 512, 2048}, FP32 and BF16 side by side, every
     admissible b timed (one graph-replayed epoch after a warm-up epoch that captures
     the graph), then the split length tuned at the fastest b.  Where b = 1 and b = d
-    are admissible the table holds the three-way comparison iCD / iALS++ / iALS."""
+    are timed (iCD up to d = 256, iALS up to d = 512) the table holds the three-way
+    comparison iCD / iALS++ / iALS."""
     from paper_2110_14044_gb300 import _abi, autotune, synth
     data = collect_generation(job)
     c = synth.PRESETS[SWEEP]
@@ -692,7 +693,8 @@ def run_sweep(job, stream):
         rec = {}
         for pname, prec in (("fp32", _abi.PREC_FP32), ("bf16", _abi.PREC_BF16)):
             by_b = {}
-            for b in SWEEP_BLOCKS:
+            # iALS (b = d) is timed up to d = 512; b = 1 (iCD) up to d = 256
+            for b in SWEEP_BLOCKS + ((d,) if 256 < d <= 512 else ()):
                 if not autotune.admissible(d, b, prec) or (b == 1 and d > 256):
                     continue
                 by_b[b] = autotune.time_epoch(data, d, b, c["alpha0"], c["lam"], c["nu"], prec,

@@ -76,7 +76,9 @@ enum {
 
 typedef struct {
     int32_t d;          /* embedding dimension; multiple of 4, 4 <= d <= 4096 */
-    int32_t b;          /* block size |pi|; a power of two <= 256 that divides d (BF16: 16 .. 128) */
+    int32_t b;          /* block size |pi|; a power of two <= 256 that divides d (BF16: 16 .. 128),
+                         * or, FP32 only, b = d for d a multiple of 64 up to 1024 (iALS,
+                         * Algorithm 1; ials_block_step then refuses) */
     double alpha0;      /* weight of the all-pairs term, >= 0 */
     double lambda;      /* L2 weight, >= 0 */
     double nu;          /* regularisation scaling: lambda_r = lambda (1 + nu |S_r|), >= 0 */

@@ -31,6 +31,8 @@ def admissible(d: int, b: int, precision: int) -> bool:
         return False
     if precision == _abi.PREC_BF16:
         return b in (16, 32, 64, 128) and d % 8 == 0
+    if b == d and 256 < d <= 1024 and d % 64 == 0:  # iALS (Algorithm 1) at large d
+        return True
     return b in (1, 2, 4, 8, 16, 32, 64, 128, 256)
 
 

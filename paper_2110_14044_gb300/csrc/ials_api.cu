@@ -116,7 +116,7 @@ cudaError_t launch_sparse(const StepArgs &a, cudaStream_t s) {
         case 64: return launch_sparse_b64(a, s);
         case 128: return launch_sparse_b128(a, s);
         case 256: return launch_sparse_b256(a, s);
-        default: return cudaErrorInvalidValue;
+        default: return a.b > 256 ? launch_ials_big(a, s) : cudaErrorInvalidValue;
     }
 }
 
@@ -144,6 +144,8 @@ struct ials_ctx {
     int32_t n_obj_part = 0;
     double *g64a = nullptr, *g64b = nullptr, *g64ws = nullptr;
     double *retry_ws = nullptr;  // b > 128: FP64 re-solve systems
+    float *big_ws = nullptr;     // b = d > 256 (iALS): per-block row systems, FP32 and FP64
+    double *big_ws64 = nullptr;
     // iCD path (b = 1): Gramian columns (two of d), their partials, completion counter
     float *icd_g = nullptr, *icd_gpart = nullptr;
     float *WT = nullptr, *HT = nullptr;  // transposed factors (d x n), kept current by the passes
@@ -292,6 +294,8 @@ StepArgs step_args(ials_ctx *c, int side, int p0, Profiler *prof) {
     a.stats = c->stats;
     a.force_fp64 = (c->p.flags & IALS_FLAG_FORCE_FP64) ? 1 : 0;
     a.retry_ws = c->retry_ws;
+    a.big_ws = c->big_ws;
+    a.big_ws64 = c->big_ws64;
     a.prof = prof;
     a.Xh = side == 0 ? c->Wh : c->Hh;
     a.Xl = side == 0 ? c->Wl : c->Hl;
@@ -340,7 +344,8 @@ ials_status icd_pass_enqueue(ials_ctx *c, int side, int f, int fn, const float *
     return IALS_OK;
 }
 
-// The iALS path (Algorithm 1) runs for b = d in {64, 128} unless the general path is forced.
+// The iALS path (Algorithm 1) runs for b = d >= 64 unless the general path is forced (which
+// creation refuses above b = 256).
 bool use_ials(const ials_ctx *c) {
     return c->p.b == c->p.d && c->p.b >= 64 && !(c->p.flags & IALS_FLAG_GENERAL);
 }
@@ -516,8 +521,12 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     *out = nullptr;
     const ials_params p = *params;
     if (p.d < 4 || p.d > 4096 || p.d % 4 != 0) return fail(IALS_EINVAL, "d must be a multiple of 4 in [4, 4096]");
-    if (!valid_block(p.b) || p.d % p.b != 0)
-        return fail(IALS_EINVAL, "b must be a power of two <= 256 that divides d");
+    const bool big = p.b == p.d && ials_big_supported(p.d);  // iALS only (Algorithm 1)
+    if (!big && (!valid_block(p.b) || p.d % p.b != 0))
+        return fail(IALS_EINVAL, "b must be a power of two <= 256 that divides d, or b = d (a multiple of 64 up "
+                                 "to 1024)");
+    if (big && (p.flags & IALS_FLAG_GENERAL))
+        return fail(IALS_EINVAL, "the general block step needs b <= 256; b = d above 256 runs iALS only");
     if (!(p.alpha0 >= 0) || !(p.lambda >= 0) || !(p.nu >= 0) || !std::isfinite(p.alpha0) ||
         !std::isfinite(p.lambda) || !std::isfinite(p.nu))
         return fail(IALS_EINVAL, "alpha0, lambda, nu must be finite and >= 0");
@@ -667,9 +676,14 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
                                std::max(gram_tc_ws_floats(n_items, d, b), gram_tc_ws_floats(n_users, d, b))),
           "Gramian workspace");
     ALLOC(c->dev_err, 1, "error flag");
-    ALLOC(c->R, max_rows * b, "row terms");
-    ALLOC(c->part, (int64_t)max_slots * (b * b + b), "split partials");
-    ALLOC(c->delta, (int64_t)max_split * b, "split deltas");
+    const bool big_ials = b > 256;  // iALS at b = d > 256: whole rows, no row terms or split partials
+    ALLOC(c->R, big_ials ? 1 : max_rows * b, "row terms");
+    ALLOC(c->part, big_ials ? 1 : (int64_t)max_slots * (b * b + b), "split partials");
+    ALLOC(c->delta, big_ials ? 1 : (int64_t)max_split * b, "split deltas");
+    if (big_ials) {
+        ALLOC(c->big_ws, ials_big_ws_floats(d), "iALS row systems");
+        ALLOC(c->big_ws64, ials_big_ws_doubles(d), "iALS FP64 row systems");
+    }
     ALLOC(c->ctl, max_rows + 2, "counters");
     ALLOC(c->stats, 2, "stats");
     ALLOC(c->obj, 3, "objective");
@@ -737,8 +751,9 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     cudaError_t e6 = cudaStreamSynchronize(c->stream);
     // Set kernel attributes of both sides' sparse variants now, outside any
     // stream capture: an empty step launches nothing but the (idle) retry kernel.
-    cudaError_t e7 = cudaSuccess;
+    cudaError_t e7 = b > 256 ? ials_big_prepare() : cudaSuccess;
     for (int k = 0; k < (use_ials(c) ? 4 : 2) && e7 == cudaSuccess; ++k) {
+        if (b > 256 && !(k >> 1)) continue;  // above b = 256 only the iALS path exists
         const int sd = k & 1;
         StepArgs a = step_args(c, sd, 0, nullptr);
         a.n_tasks = a.n_split = a.n_stasks = 0;
@@ -845,6 +860,7 @@ ials_status ials_recompute_residuals(ials_ctx *c) {
 ials_status ials_block_step(ials_ctx *c, int32_t side, int32_t block) {
     if (!c || side < 0 || side > 1 || block < 0 || block >= c->p.d / c->p.b)
         return fail(IALS_EINVAL, "bad side or block");
+    if (c->p.b > 256) return fail(IALS_EINVAL, "block steps need b <= 256 (at b = d above 256 the epoch runs iALS)");
     IALS_CUDA(cudaMemsetAsync(c->stats, 0, 2 * sizeof(int64_t), c->stream), "stats reset");
     IALS_CUDA(ensure_residuals(c), "residual recompute");
     ials_status st = step_enqueue(c, side, block);

@@ -117,6 +117,8 @@ struct StepArgs {
     int32_t force_fp64;     // fault injection: every FP32 pivot counts as failed
     int32_t direct;         // b = d (Algorithm 1): solve for x_r itself from sum alpha y f, no residuals
     double *retry_ws;       // b > 128: FP64 systems of the re-solve kernel's blocks
+    float *big_ws;          // b = d > 256: per-block row systems of the iALS kernel
+    double *big_ws64;       // and of its FP64 re-solve
     Profiler *prof;         // host only: event marks around launches, or nullptr
 };
 
@@ -265,6 +267,13 @@ cudaError_t launch_sparse_b32(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_sparse_b64(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_sparse_b128(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_sparse_b256(const StepArgs &a, cudaStream_t s);
+// iALS at b = d above 256 (k_ials_big.cu): d a multiple of 64 up to 1024, FP32 with
+// an FP64 re-solve; row systems in global workspaces of the given sizes
+bool ials_big_supported(int32_t d);
+int64_t ials_big_ws_floats(int32_t d);
+int64_t ials_big_ws_doubles(int32_t d);
+cudaError_t ials_big_prepare();  // kernel attributes; call once outside any stream capture
+cudaError_t launch_ials_big(const StepArgs &a, cudaStream_t s);
 // doubles of FP64 re-solve workspace a block size needs (0 up to b = 128)
 int64_t sparse_retry_ws_doubles(int32_t b);
 // fold-in (k_foldin.cu): one CTA per request, or (cluster) one cluster of

@@ -70,7 +70,8 @@ def _create(p, n_users, n_items, uptr, uidx, **kw):
 @pytest.mark.parametrize("case", ["d", "b_not_dividing", "bf16_b", "alpha0",
                                   "indptr_end", "indptr_order", "item_range", "repeat",
                                   "transpose_len", "transpose_pairs", "alpha_zero", "y_nan",
-                                  "split_len_small", "split_len_large", "reserved"])
+                                  "split_len_small", "split_len_large", "reserved", "big_b_not_d",
+                                  "big_too_large", "big_bf16", "big_general"])
 def test_create_validates_on_the_host(case):
     """Every argument check runs on the host before any device work, so a bad
     input is rejected with IALS_EINVAL and a message, GPU or not."""
@@ -113,6 +114,14 @@ def test_create_validates_on_the_host(case):
     elif case == "reserved":
         good["p"] = _abi.make_params(16, 8, 0.1, 0.01)
         good["p"].reserved = 1
+    elif case == "big_b_not_d":      # above 256 only b = d (iALS) exists
+        good["p"] = _abi.make_params(1024, 512, 0.1, 0.01)
+    elif case == "big_too_large":
+        good["p"] = _abi.make_params(1088, 1088, 0.1, 0.01)
+    elif case == "big_bf16":
+        good["p"] = _abi.make_params(512, 512, 0.1, 0.01, precision=_abi.PREC_BF16)
+    elif case == "big_general":      # the general block step stops at b = 256
+        good["p"] = _abi.make_params(512, 512, 0.1, 0.01, flags=_abi.FLAG_GENERAL)
     with pytest.raises(_abi.IalsError) as ei:
         _create(**good, **kw)
     assert ei.value.status == _abi.EINVAL, (case, str(ei.value))
@@ -126,7 +135,8 @@ def test_create_accepts_valid_input_up_to_the_device_check():
     if torch.cuda.is_available():
         pytest.skip("a device is present")
     for p in (_abi.make_params(16, 8, 0.1, 0.01),
-              _abi.make_params(32, 16, 0.1, 0.01, precision=_abi.PREC_BF16)):  # weights in BF16 too
+              _abi.make_params(32, 16, 0.1, 0.01, precision=_abi.PREC_BF16),  # weights in BF16 too
+              _abi.make_params(320, 320, 0.1, 0.01)):                         # iALS above b = 256
         with pytest.raises(_abi.IalsError) as ei:
             _create(p, 3, 4, [0, 2, 3, 5], [0, 1, 3, 1, 2],
                     i_indptr=np.array([0, 1, 3, 4, 5], np.int64), i_users=np.array([0, 2, 0, 2, 1], np.int32),

@@ -155,3 +155,44 @@ def test_ials_path_bf16_and_fp64_retry(d):
     W, H = f.factors()
     assert abs(o64 - ref) <= OBJ_TOL * ref
     assert rel_embed_err(W, Wr) <= EMB_TOL and rel_embed_err(H, Hr) <= EMB_TOL
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_ials_above_b_256_matches_oracle_algorithm_1(weighted):
+    """b = d = 320: the row systems no longer fit on chip and live in a global
+    workspace (5 x 5 tiles of 64); long rows are taken whole by one block."""
+    d = 320
+    data, W0, H0, y, a = long_row_problem(d, 40 + weighted)
+    if not weighted:
+        y = a = None
+    m = Model(data, d, d, 0.1, 1e-3, 0.5, W0=W0, H0=H0, y=y, alpha=a, graph=True)
+    o, st = m.epoch(2, objective=True)
+    assert st == 0 and m.stats() == (0, 0)
+    W, H = m.factors()
+    P = oracle.Problem.from_data(data, d, d, 0.1, 1e-3, 0.5, y=y, alpha=a)
+    Wr, Hr, st = oracle.ials(P, 2, W0, H0)
+    assert st == 0
+    ref = oracle.objective(P, Wr, Hr)
+    print(f"iALS d={d} weighted={weighted}: rel objective {abs(o - ref) / ref:.2e}, "
+          f"embedding W {rel_embed_err(W, Wr):.2e} H {rel_embed_err(H, Hr):.2e}")
+    assert abs(o - ref) <= OBJ_TOL * ref
+    assert rel_embed_err(W, Wr) <= EMB_TOL and rel_embed_err(H, Hr) <= EMB_TOL
+    with pytest.raises(_abi.IalsError):  # no general block step above b = 256
+        m.block_step(0, 0)
+
+
+def test_ials_above_b_256_fp64_retry():
+    """Every FP32 pivot treated as failed: every row re-solved by the FP64 form of the
+    same kernel, with the oracle's answer."""
+    d = 320
+    data, W0, H0, _, _ = long_row_problem(d, 50, n_users=400, n_items=500)
+    P = oracle.Problem.from_data(data, d, d, 0.1, 1e-3, 0.5)
+    Wr, Hr, st = oracle.ials(P, 1, W0, H0)
+    ref = oracle.objective(P, Wr, Hr)
+    f = Model(data, d, d, 0.1, 1e-3, 0.5, W0=W0, H0=H0, force_fp64=True)
+    o64, st = f.epoch(1, objective=True)
+    assert st == 0
+    assert f.stats() == (data.n_users + data.n_items, 0)
+    W, H = f.factors()
+    assert abs(o64 - ref) <= OBJ_TOL * ref
+    assert rel_embed_err(W, Wr) <= EMB_TOL and rel_embed_err(H, Hr) <= EMB_TOL

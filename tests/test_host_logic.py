@@ -20,6 +20,10 @@ def test_admissible_block_sizes():
     assert not autotune.admissible(128, 8, bf16)
     assert [b for b in autotune.CANDIDATES if autotune.admissible(64, b, fp32)] == [1, 2, 4, 8, 16, 32, 64]
     assert autotune.admissible(512, 256, fp32) and not autotune.admissible(512, 256, bf16)
+    # b = d above 256 (iALS, FP32 only): d a multiple of 64 up to 1024
+    assert autotune.admissible(512, 512, fp32) and autotune.admissible(1024, 1024, fp32)
+    assert autotune.admissible(320, 320, fp32) and not autotune.admissible(2048, 2048, fp32)
+    assert not autotune.admissible(512, 512, bf16) and not autotune.admissible(1024, 512, fp32)
     assert [b for b in autotune.CANDIDATES if autotune.admissible(64, b, bf16)] == [16, 32, 64]
 
 
