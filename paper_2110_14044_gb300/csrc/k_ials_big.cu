@@ -129,16 +129,17 @@ __device__ bool big_row(const StepArgs &a, T *A, T *gv, T *xv, T *dg, T *sm, int
         }
         __syncthreads();
         for (int c = 0; c < BT; ++c) {
+            // every thread takes the pivot (written by the previous column's update);
+            // thread 0 checks it and stores the factor's diagonal after the barrier
+            const T dc = D[c * SP + c];
+            const T l = big_sqrt(dc > (T)0 ? dc : (T)1), il = (T)1 / l;
+            if (tid == 0 && (!(dc > rel * dg[p * BT + c]) || !big_finite(dc))) *bad = 1;
+            for (int r = c + 1 + tid; r < BT; r += BTH) D[r * SP + c] *= il;
+            __syncthreads();
             if (tid == 0) {
-                const T dc = D[c * SP + c];
-                if (!(dc > rel * dg[p * BT + c]) || !big_finite(dc)) *bad = 1;
-                const T l = big_sqrt(dc > (T)0 ? dc : (T)1);
                 D[c * SP + c] = l;
-                inv[c] = (T)1 / l;
+                inv[c] = il;
             }
-            __syncthreads();
-            for (int r = c + 1 + tid; r < BT; r += BTH) D[r * SP + c] *= inv[c];
-            __syncthreads();
             const int m = BT - 1 - c;
             for (int f = tid; f < m * m; f += BTH) {
                 const int r = c + 1 + f / m, s = c + 1 + f % m;
@@ -231,28 +232,32 @@ __device__ bool big_row(const StepArgs &a, T *A, T *gv, T *xv, T *dg, T *sm, int
         }
     }
     if (*bad) return false;  // uniform: set before the last barrier
-    // ---- forward substitution L y = g (y overwrites g)
+    // ---- forward substitution L y = g (y overwrites g); the diagonal block staged in D
     const int r64 = tid & (BT - 1), part = tid >> 6;
     for (int p = 0; p < nt; ++p) {
-        T t = 0;
-        const T *lrow = A + (int64_t)(p * BT + r64) * d;
-        for (int c = part; c < p * BT; c += 4) t += lrow[c] * gv[c];
-        red[part * BT + r64] = t;
-        __syncthreads();
-        if (tid < BT) blk[tid] = gv[p * BT + tid] - (((red[tid] + red[BT + tid]) + red[2 * BT + tid]) + red[3 * BT + tid]);
-        __syncthreads();
-        if (warp == 0) {  // L_pp y_p = blk, row by row
-            for (int r = 0; r < BT; ++r) {
-                T s = 0;
-                for (int mm = lane; mm < r; mm += 32) s += A[(int64_t)(p * BT + r) * d + p * BT + mm] * blk[mm];
+        for (int r = warp; r < BT; r += BTH / 32) {  // rows of block p against y of the blocks before
+            const T *lrow = A + (int64_t)(p * BT + r) * d;
+            T t = 0;
+            for (int c = lane; c < p * BT; c += 32) t += lrow[c] * gv[c];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-                if (lane == 0) blk[r] = (blk[r] - s) / A[(int64_t)(p * BT + r) * d + p * BT + r];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+            if (lane == 0) red[r] = t;
+        }
+        for (int f = tid; f < BT * BT; f += BTH) {
+            const int r = f / BT, c = f % BT;
+            D[r * SP + c] = A[(int64_t)(p * BT + r) * d + p * BT + c];
+        }
+        __syncthreads();
+        if (warp == 0) {  // L_pp y_p = g_p - (L y)_p, row by row
+            for (int r = 0; r < BT; ++r) {
+                T t = 0;
+                for (int mm = lane; mm < r; mm += 32) t += D[r * SP + mm] * gv[p * BT + mm];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+                if (lane == 0) gv[p * BT + r] = (gv[p * BT + r] - red[r] - t) / D[r * SP + r];
                 __syncwarp();
             }
         }
-        __syncthreads();
-        if (tid < BT) gv[p * BT + tid] = blk[tid];
         __syncthreads();
     }
     // ---- backward substitution L^T x = y
@@ -260,16 +265,20 @@ __device__ bool big_row(const StepArgs &a, T *A, T *gv, T *xv, T *dg, T *sm, int
         T t = 0;
         for (int c = (p + 1) * BT + part; c < d; c += 4) t += A[(int64_t)c * d + p * BT + r64] * xv[c];
         red[part * BT + r64] = t;
+        for (int f = tid; f < BT * BT; f += BTH) {
+            const int r = f / BT, c = f % BT;
+            D[r * SP + c] = A[(int64_t)(p * BT + r) * d + p * BT + c];
+        }
         __syncthreads();
         if (tid < BT) blk[tid] = gv[p * BT + tid] - (((red[tid] + red[BT + tid]) + red[2 * BT + tid]) + red[3 * BT + tid]);
         __syncthreads();
         if (warp == 0) {  // L_pp^T x_p = blk, from the last row
             for (int r = BT - 1; r >= 0; --r) {
-                T s = 0;
-                for (int mm = r + 1 + lane; mm < BT; mm += 32) s += A[(int64_t)(p * BT + mm) * d + p * BT + r] * blk[mm];
+                T t2 = 0;
+                for (int mm = r + 1 + lane; mm < BT; mm += 32) t2 += D[mm * SP + r] * blk[mm];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-                if (lane == 0) blk[r] = (blk[r] - s) / A[(int64_t)(p * BT + r) * d + p * BT + r];
+                for (int o = 16; o > 0; o >>= 1) t2 += __shfl_xor_sync(kFull, t2, o);
+                if (lane == 0) blk[r] = (blk[r] - t2) / D[r * SP + r];
                 __syncwarp();
             }
         }
