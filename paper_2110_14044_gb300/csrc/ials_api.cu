@@ -92,6 +92,10 @@ struct SideDev {
     int64_t *ptr = nullptr;
     int32_t *idx = nullptr;
     int32_t *pos = nullptr;  // item side only
+    // item side: user-major positions whose item is a split row (increasing) and
+    // the split row of each, for the residual update in user-major order
+    int32_t *split_pos = nullptr, *split_row = nullptr;
+    int64_t n_spos = 0;
     Task *tasks = nullptr;
     int32_t n_tasks = 0;
     SplitRow *split = nullptr;
@@ -297,6 +301,13 @@ StepArgs step_args(ials_ctx *c, int side, int p0, Profiler *prof) {
     a.big_ws = c->big_ws;
     a.big_ws64 = c->big_ws64;
     a.prof = prof;
+    if (side == 1 && sd.split_pos) {
+        a.optr = c->side[0].ptr;
+        a.split_pos = sd.split_pos;
+        a.split_row = sd.split_row;
+        a.n_spos = sd.n_spos;
+        a.n_orows = c->n_users;
+    }
     a.Xh = side == 0 ? c->Wh : c->Hh;
     a.Xl = side == 0 ? c->Wl : c->Hl;
     a.Fh = side == 0 ? c->Hh : c->Wh;
@@ -660,6 +671,15 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
         ALLOC(S.ptr, (int64_t)S.n_rows + 1, "CSR indptr");
         ALLOC(S.idx, nnz, "CSR indices");
         if (sd == 1) ALLOC(S.pos, nnz, "position map");
+        // the item side's split rows update their residuals in user-major order
+        // when they hold at least an eighth of the interactions
+        if (sd == 1 && b % 8 == 0 && b <= 256 && !(b == d && b >= 64 && !(p.flags & IALS_FLAG_GENERAL)) &&
+            !ht[1].split.empty() && c->nnz_split[1] * 8 >= nnz)
+        {
+            S.n_spos = c->nnz_split[1];
+            ALLOC(S.split_pos, S.n_spos, "split positions");
+            ALLOC(S.split_row, S.n_spos, "split rows of the positions");
+        }
         S.n_tasks = (int32_t)ht[sd].tasks.size();
         S.n_split = (int32_t)ht[sd].split.size();
         S.n_stasks = (int32_t)ht[sd].stasks.size();
@@ -719,6 +739,20 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
     up(iptr.data(), c->side[1].ptr, sizeof(int64_t) * (n_items + 1), "item indptr");
     up(iidx.data(), c->side[1].idx, sizeof(int32_t) * nnz, "item users");
     up(ipos.data(), c->side[1].pos, sizeof(int32_t) * nnz, "position map");
+    if (c->side[1].split_pos) {
+        std::vector<int32_t> sq(nnz, -1);
+        for (size_t r = 0; r < ht[1].split.size(); ++r) {
+            const SplitRow &sr = ht[1].split[r];
+            for (int64_t t = sr.begin; t < sr.begin + sr.len; ++t) sq[ipos[t]] = (int32_t)r;
+        }
+        std::vector<int32_t> lp, lr;
+        lp.reserve(c->side[1].n_spos);
+        lr.reserve(c->side[1].n_spos);
+        for (int64_t q = 0; q < nnz; ++q)
+            if (sq[q] >= 0) { lp.push_back((int32_t)q); lr.push_back(sq[q]); }
+        up(lp.data(), c->side[1].split_pos, sizeof(int32_t) * lp.size(), "split positions");
+        up(lr.data(), c->side[1].split_row, sizeof(int32_t) * lr.size(), "split rows of the positions");
+    }
     if (y) up(hy.data(), c->y, sizeof(float) * nnz, "y");
     if (alpha) up(ha.data(), c->alpha, sizeof(float) * nnz, "alpha");
     for (int sd = 0; sd < 2; ++sd) {
@@ -947,8 +981,11 @@ ials_status ials_work_model(ials_ctx *c, double *bytes, double *flops, int32_t n
                              r_u * (b * b * b / 3 + 2 * b * b));
         B[K_SPLIT_SOLVE] += nb * (S.n_slots * (b * b + b) * 4 + S.n_split * (4 * b + 12 * b + 24));
         F[K_SPLIT_SOLVE] += nb * (S.n_slots * (b * b + b) + S.n_split * (b * b * b / 3 + 2 * b * b));
-        B[K_SPLIT_RESID] += nb * (nz_s * (4 + 4 * b + 8 + (sd == 1 ? 4 : 0)) +
-                                  S.n_stasks * ((double)sizeof(Task) + 4 * b));
+        if (S.split_pos && (int64_t)S.n_split * b * 4 <= kScanSmemMax)  // user-major list
+            B[K_SPLIT_RESID] += nb * (nz_s * (8 + 8) + nu * (8 + 4 * b) + S.n_split * 4.0 * b);
+        else
+            B[K_SPLIT_RESID] += nb * (nz_s * (4 + 4 * b + 8 + (sd == 1 ? 4 : 0)) +
+                                      S.n_stasks * ((double)sizeof(Task) + 4 * b));
         F[K_SPLIT_RESID] += nb * nz_s * 2 * b;
     }
     for (int k = 0; k < n_kinds; ++k) {

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -64,6 +65,8 @@ __device__ __forceinline__ void apply_delta(float *X, __nv_bfloat16 *Xh, __nv_bf
 
 constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
+// shared memory for the delta table of the user-major split-row residual scan
+constexpr int kScanSmemMax = 200 * 1024;
 
 // One unit of sparse work: a whole row, or a chunk of a long ("split") row.
 struct Task {
@@ -119,6 +122,13 @@ struct StepArgs {
     double *retry_ws;       // b > 128: FP64 systems of the re-solve kernel's blocks
     float *big_ws;          // b = d > 256: per-block row systems of the iALS kernel
     double *big_ws64;       // and of its FP64 re-solve
+    // item side with split rows: the user-major view, for the split rows' residual
+    // update in user-major order (nullptr / 0 otherwise)
+    const int64_t *optr;      // user CSR row pointers (n_orows + 1)
+    const int32_t *split_pos; // user-major positions whose item is a split row, increasing
+    const int32_t *split_row; // the split row of each
+    int64_t n_spos;           // entries of the two lists
+    int32_t n_orows;          // users
     Profiler *prof;         // host only: event marks around launches, or nullptr
 };
 

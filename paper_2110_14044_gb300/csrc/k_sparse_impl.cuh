@@ -24,6 +24,7 @@
 #pragma once
 
 #include "ials_internal.cuh"
+#include "k_split_resid_scan.cuh"
 
 namespace ials {
 
@@ -952,6 +953,11 @@ cudaError_t launch_split_resid_reg_bf16(const StepArgs &a, cudaStream_t s) {
         if (err != cudaSuccess) return err;
         per_sm = n > 0 ? n : 1;
     }
+    if constexpr (PERM && B % 8 == 0) {  // item side: the user-major scan where it applies
+        cudaError_t err = split_scan_prepare<B, true>(nullptr);
+        if (err != cudaSuccess) return err;
+        if (split_scan_applies<B>(a)) return launch_split_resid_scan<B, true>(a, s);
+    }
     if (a.n_stasks <= 0) return cudaSuccess;
     cudaError_t err = cudaMemsetAsync(a.counter, 0, sizeof(int32_t), s);
     if (err != cudaSuccess) return err;
@@ -972,6 +978,11 @@ cudaError_t launch_split_resid_reg(const StepArgs &a, cudaStream_t s) {
         cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_split_resid_reg<B, PERM>, 256, 0);
         if (err != cudaSuccess) return err;
         per_sm = n > 0 ? n : 1;
+    }
+    if constexpr (PERM && B % 8 == 0) {  // item side: the user-major scan where it applies
+        cudaError_t err = split_scan_prepare<B, false>(nullptr);
+        if (err != cudaSuccess) return err;
+        if (split_scan_applies<B>(a)) return launch_split_resid_scan<B, false>(a, s);
     }
     if (a.n_stasks <= 0) return cudaSuccess;
     cudaError_t err = cudaMemsetAsync(a.counter, 0, sizeof(int32_t), s);

@@ -487,6 +487,46 @@ def test_short_split_length_matches_oracle(split_len, precision, d, b):
     assert rel_embed_err(W, Wr) <= tol_emb and rel_embed_err(H, Hr) <= tol_emb
 
 
+@pytest.mark.parametrize("precision,d,b", [(_abi.PREC_FP32, 64, 8), (_abi.PREC_FP32, 64, 32),
+                                           (_abi.PREC_BF16, 64, 32), (_abi.PREC_FP32, 128, 64),
+                                           (_abi.PREC_BF16, 128, 64), (_abi.PREC_FP32, 256, 128),
+                                           (_abi.PREC_BF16, 256, 128)])
+def test_split_item_rows_update_residuals_in_user_order(precision, d, b):
+    """Item rows cut into chunks that hold most interactions update their residuals
+    in one user-major scan.  Users without interactions sit between active ones,
+    at both ends and in a run of 40 (more than the 32 user boundaries a warp reads
+    at a time).  The residual cache after the epoch equals the residuals
+    recomputed from the factors, and the epoch matches the oracle."""
+    rng = np.random.default_rng(70 + b)
+    n_users, n_items = 1500, 300
+    active = np.ones(n_users, bool)
+    active[rng.choice(n_users, 150, replace=False)] = False
+    active[600:640] = False
+    active[0] = active[-1] = False
+    mask = (rng.random((n_users, n_items)) < 0.08) & active[:, None]
+    mask[active, 3] = True  # one item held by every active user
+    u, i = np.nonzero(mask)
+    data = synth.from_pairs(n_users, n_items, u, i)
+    assert np.diff(data.i_indptr).min() > 32  # every item row is split at split_len = 32
+    W0, H0 = synth.init_factors(n_users, n_items, d, 0.1 / np.sqrt(d), 80 + b)
+    m = Model(data, d, b, 0.1, 1e-3, 1.0, precision=precision, W0=W0, H0=H0, split_len=32)
+    o, st = m.epoch(1, objective=True)
+    assert st == 0
+    W, H = m.factors()
+    P = oracle.Problem.from_data(data, d, b, 0.1, 1e-3, 1.0)
+    e = m.residuals().astype(np.float64)
+    ref_e = oracle.predict(P, W, H) - 1.0
+    res_tol = 1e-4 if precision == _abi.PREC_FP32 else 1e-3
+    assert np.abs(e - ref_e).max() <= res_tol * max(1.0, np.abs(ref_e).max())
+    Wr, Hr, _, _, _ = oracle.ialspp(P, 1, W0, H0)
+    ref = oracle.objective(P, Wr, Hr)
+    tol_obj, tol_emb = (OBJ_TOL, EMB_TOL) if precision == _abi.PREC_FP32 else (1e-3, 5e-2)
+    print(f"d={d} b={b} prec={precision}: rel objective {abs(o - ref) / ref:.2e}, "
+          f"residual cache {np.abs(e - ref_e).max():.2e}")
+    assert abs(o - ref) / ref <= tol_obj
+    assert rel_embed_err(W, Wr) <= tol_emb and rel_embed_err(H, Hr) <= tol_emb
+
+
 @pytest.mark.parametrize("b,precision", [(16, _abi.PREC_FP32), (64, _abi.PREC_FP32), (32, _abi.PREC_BF16)])
 def test_skewed_user_activity_epochs(b, precision):
     """Zipf(1.3) user activity with rows capped at the whole catalogue (the skewed
