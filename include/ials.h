@@ -62,7 +62,10 @@ enum {
                           * products hi*hi + hi*lo + lo*hi accumulated in FP32 (about 16
                           * bits); weighted interactions enter as rows scaled by
                           * sqrt(alpha); FP32 solve with FP64 retry, FP64 objective.
-                          * Needs b in {16, 32, 64, 128} and d % 8 == 0. */
+                          * At b = 128 the row statistics are FP32 (register tiles,
+                          * measured faster there); the Gramian and row terms stay
+                          * on the tensor cores.  Needs b in {16, 32, 64, 128} and
+                          * d % 8 == 0. */
 };
 
 /* ials_params.flags */
