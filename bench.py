@@ -352,7 +352,8 @@ def kernel_rooflines(m, steps, prec, b, precision_name, workload_key, peaks):
     # measured copy bandwidth; FLOPs against the tensor peak (BF16 tensor-core kernels: the
     # measured burst bf16 peak) or the FP32 FMA peak (152 SMs x 128 FMA x 2 x max SM clock)
     fma_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    tensor_kinds = ("gram", "rowterm", "sparse") if prec == _abi.PREC_BF16 else ()
+    # (the BF16 path's row statistics at b = 128 run on FP32 register tiles)
+    tensor_kinds = (("gram", "rowterm") + (("sparse",) if b != 128 else ())) if prec == _abi.PREC_BF16 else ()
     per_kind = {}
     for k, (kms, kcnt) in kern.items():
         if kms <= 0 or k == "objective":
