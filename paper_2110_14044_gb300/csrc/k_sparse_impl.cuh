@@ -682,11 +682,14 @@ __global__ void __launch_bounds__(256, 2) k_sparse_tiled(const StepArgs a) {
 }
 
 // One block per split row: 256 threads sum the partial slots of the row in
-// slot order (thread t owns elements t, t + 256, ...), then warp 0 adds the
-// dense terms, solves and applies.
+// slot order (thread t owns elements t, t + 256, ...; its elements' sums run side
+// by side so that the loads of several slots are in flight at once), then warp 0
+// adds the dense terms, solves (the warp Gauss-Jordan elimination of the unsplit
+// rows; Cholesky below b = 4) and applies.
 template <int B>
-__global__ void __launch_bounds__(256) k_split_solve(const StepArgs a) {
+__global__ void __launch_bounds__(256, 2) k_split_solve(const StepArgs a) {
     constexpr int NE = B * B + B;
+    constexpr int PER = (NE + 255) / 256;
     extern __shared__ float4 smem4[];
     float *red = reinterpret_cast<float *>(smem4);
     WarpSmem w;
@@ -697,10 +700,22 @@ __global__ void __launch_bounds__(256) k_split_solve(const StepArgs a) {
     for (int i = blockIdx.x; i < a.n_split; i += gridDim.x) {
         const SplitRow sr = a.split[i];
         const float *P0 = a.part + (int64_t)sr.slot0 * NE;
-        for (int e = threadIdx.x; e < NE; e += blockDim.x) {
-            float t = 0.f;
-            for (int sl = 0; sl < sr.nslots; ++sl) t += P0[(int64_t)sl * NE + e];
-            red[e] = t;
+        float t[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) t[k] = 0.f;
+#pragma unroll 4
+        for (int sl = 0; sl < sr.nslots; ++sl) {
+            const float *P = P0 + (int64_t)sl * NE;
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                const int e = threadIdx.x + 256 * k;
+                if (e < NE) t[k] += P[e];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = threadIdx.x + 256 * k;
+            if (e < NE) red[e] = t[k];
         }
         __syncthreads();
         if (warp == 0) {
@@ -714,7 +729,9 @@ __global__ void __launch_bounds__(256) k_split_solve(const StepArgs a) {
                 acc[j] += a.alpha0 * a.G[(int64_t)(a.p0 + max(j, col)) * B + min(j, col)] + (j == col ? lam : 0.f);
             g += a.R[(int64_t)sr.row * B + col];
             float delta = 0.f;
-            const bool ok = chol_solve<B>(acc, g, col, sub, w, a.force_fp64 != 0, delta);
+            bool ok;
+            if constexpr (B % 4 == 0) ok = gj_solve2<B>(acc, g, col, sub, w, a.force_fp64 != 0, delta);
+            else ok = chol_solve<B>(acc, g, col, sub, w, a.force_fp64 != 0, delta);
             if (!ok) {
                 queue_retry(a, lane, sr.row);
                 delta = 0.f;  // k_split_resid leaves the row's residuals alone
