@@ -200,11 +200,12 @@ __global__ void __launch_bounds__(256, 2) k_sparse_bf16(const StepArgs a) {
     w.v = vv;
     w.L = As;
     const int col = lane % B, sub = lane / B;
+    int nxt = 0;  // lane 0: the next task index, fetched while the current task runs
+    if (lane == 0) nxt = atomicAdd(a.counter, 1);
     for (;;) {
-        int tsk = 0;
-        if (lane == 0) tsk = atomicAdd(a.counter, 1);
-        tsk = __shfl_sync(kFull, tsk, 0);
+        const int tsk = __shfl_sync(kFull, nxt, 0);
         if (tsk >= a.n_tasks) break;
+        if (lane == 0) nxt = atomicAdd(a.counter, 1);
         const Task tk = a.tasks[tsk];
         const int nch = (tk.len + CH - 1) / CH;
         float acc[C::NLOW][4], gac[MT][4];
