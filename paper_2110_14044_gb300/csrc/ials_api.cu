@@ -674,8 +674,7 @@ ials_status ials_create(const ials_params *params, int32_t n_users, int32_t n_it
         // the item side's split rows update their residuals in user-major order
         // when they hold at least an eighth of the interactions
         if (sd == 1 && b % 8 == 0 && b <= 256 && !(b == d && b >= 64 && !(p.flags & IALS_FLAG_GENERAL)) &&
-            !ht[1].split.empty() && c->nnz_split[1] * 8 >= nnz)
-        {
+            !ht[1].split.empty() && c->nnz_split[1] * 8 >= nnz) {
             S.n_spos = c->nnz_split[1];
             ALLOC(S.split_pos, S.n_spos, "split positions");
             ALLOC(S.split_row, S.n_spos, "split rows of the positions");
