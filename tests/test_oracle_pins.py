@@ -402,3 +402,41 @@ def test_foldin_with_precomputed_gramian_is_the_same_computation():
     w2, s2 = oracle.foldin(H, 12, 4, 0.1, 1e-2, 0.5, 3, items, y=y, G=G)
     assert s1 == s2 == 0
     assert np.array_equal(w1, w2)
+
+
+def test_relabelling_users_and_items_permutes_the_iterates():
+    """Rows of one side are solved independently (Section 3.2), so renaming users
+    and items only renames the result: a mix-up of user and item ids, or of the
+    item-major to user-major position map, breaks this."""
+    data, y, alpha, W, H = tiny(n_users=25, n_items=18, d=6, seed=31)
+    rng = np.random.default_rng(32)
+    pu, pi = rng.permutation(data.n_users), rng.permutation(data.n_items)
+    users = np.repeat(np.arange(data.n_users), np.diff(data.u_indptr))
+    nu_, ni_ = pu[users], pi[np.asarray(data.u_items)]
+    order = np.lexsort((ni_, nu_))  # the relabelled problem's user-major order
+    data2 = synth.from_pairs(data.n_users, data.n_items, nu_, ni_)
+    y2, a2 = np.asarray(y)[order], np.asarray(alpha)[order]
+    W2, H2 = np.empty_like(W), np.empty_like(H)
+    W2[pu], H2[pi] = W, H
+    Wa, Ha, _, _, st = oracle.ialspp(make(data, y, alpha, 6, 2, 0.2, 0.04, 0.5), 2, W, H)
+    Wb, Hb, _, _, st2 = oracle.ialspp(make(data2, y2, a2, 6, 2, 0.2, 0.04, 0.5), 2, W2, H2)
+    assert st == 0 and st2 == 0
+    np.testing.assert_allclose(Wb[pu], Wa, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(Hb[pi], Ha, rtol=1e-9, atol=1e-12)
+
+
+def test_scaling_every_weight_leaves_the_iterates_unchanged():
+    """Every term of Eq. 2 carries one of alpha_s, alpha0 or lambda_r, so scaling all
+    three by c scales the loss by c and leaves every Newton step (Eq. 9: g and A of
+    Eqs. 11-12 both scale by c) and so every iterate unchanged.  A term that misses
+    its weight in the gradient or the Hessian breaks this."""
+    data, y, alpha, W, H = tiny(n_users=25, n_items=18, d=6, seed=33)
+    c = 3.7
+    Pa = make(data, y, alpha, 6, 3, 0.2, 0.04, 0.5)
+    Pb = make(data, y, np.asarray(alpha) * c, 6, 3, 0.2 * c, 0.04 * c, 0.5)
+    Wa, Ha, _, _, st = oracle.ialspp(Pa, 2, W, H)
+    Wb, Hb, _, _, st2 = oracle.ialspp(Pb, 2, W, H)
+    assert st == 0 and st2 == 0
+    np.testing.assert_allclose(Wb, Wa, rtol=1e-10, atol=1e-13)
+    np.testing.assert_allclose(Hb, Ha, rtol=1e-10, atol=1e-13)
+    assert abs(oracle.objective(Pb, Wb, Hb) - c * oracle.objective(Pa, Wa, Ha)) <= 1e-10 * c * oracle.objective(Pa, Wa, Ha)
