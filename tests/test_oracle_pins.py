@@ -404,10 +404,11 @@ def test_foldin_with_precomputed_gramian_is_the_same_computation():
     assert np.array_equal(w1, w2)
 
 
-def test_relabelling_users_and_items_permutes_the_iterates():
+@pytest.mark.parametrize("algo", ["ialspp", "ials", "icd"])
+def test_relabelling_users_and_items_permutes_the_iterates(algo):
     """Rows of one side are solved independently (Section 3.2), so renaming users
-    and items only renames the result: a mix-up of user and item ids, or of the
-    item-major to user-major position map, breaks this."""
+    and items only renames the result, for Algorithms 1-3 alike: a mix-up of user
+    and item ids, or of the item-major to user-major position map, breaks this."""
     data, y, alpha, W, H = tiny(n_users=25, n_items=18, d=6, seed=31)
     rng = np.random.default_rng(32)
     pu, pi = rng.permutation(data.n_users), rng.permutation(data.n_items)
@@ -418,8 +419,15 @@ def test_relabelling_users_and_items_permutes_the_iterates():
     y2, a2 = np.asarray(y)[order], np.asarray(alpha)[order]
     W2, H2 = np.empty_like(W), np.empty_like(H)
     W2[pu], H2[pi] = W, H
-    Wa, Ha, _, _, st = oracle.ialspp(make(data, y, alpha, 6, 2, 0.2, 0.04, 0.5), 2, W, H)
-    Wb, Hb, _, _, st2 = oracle.ialspp(make(data2, y2, a2, 6, 2, 0.2, 0.04, 0.5), 2, W2, H2)
+    b = {"ialspp": 2, "ials": 6, "icd": 1}[algo]
+
+    def run(dat, yy, aa, W0, H0):
+        P = make(dat, yy, aa, 6, b, 0.2, 0.04, 0.5)
+        out = getattr(oracle, algo)(P, 2, W0, H0)
+        return out[0], out[1], out[-1]
+
+    Wa, Ha, st = run(data, y, alpha, W, H)
+    Wb, Hb, st2 = run(data2, y2, a2, W2, H2)
     assert st == 0 and st2 == 0
     np.testing.assert_allclose(Wb[pu], Wa, rtol=1e-9, atol=1e-12)
     np.testing.assert_allclose(Hb[pi], Ha, rtol=1e-9, atol=1e-12)
@@ -440,3 +448,23 @@ def test_scaling_every_weight_leaves_the_iterates_unchanged():
     np.testing.assert_allclose(Wb, Wa, rtol=1e-10, atol=1e-13)
     np.testing.assert_allclose(Hb, Ha, rtol=1e-10, atol=1e-13)
     assert abs(oracle.objective(Pb, Wb, Hb) - c * oracle.objective(Pa, Wa, Ha)) <= 1e-10 * c * oracle.objective(Pa, Wa, Ha)
+
+
+def test_foldin_does_not_depend_on_item_names_or_history_order():
+    """Fold-in (Section 5.1.1: a new user's embedding against frozen item factors)
+    sums over the request's history, so renaming the items (with H's rows) or
+    listing the history in another order changes nothing but rounding."""
+    rng = np.random.default_rng(34)
+    n_items, d = 40, 6
+    H = rng.normal(0, 0.5, (n_items, d))
+    items = rng.choice(n_items, 15, replace=False)
+    yy, aa = rng.uniform(0.5, 2, 15), rng.uniform(0.5, 2, 15)
+    w, st = oracle.foldin(H, d, 2, 0.2, 0.05, 0.5, 3, items, y=yy, alpha=aa)
+    assert st == 0
+    pi = rng.permutation(n_items)
+    H2 = np.empty_like(H)
+    H2[pi] = H
+    order = rng.permutation(15)
+    w2, st2 = oracle.foldin(H2, d, 2, 0.2, 0.05, 0.5, 3, pi[items][order], y=yy[order], alpha=aa[order])
+    assert st2 == 0
+    np.testing.assert_allclose(w2, w, rtol=1e-10, atol=1e-12)
