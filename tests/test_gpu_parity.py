@@ -527,6 +527,47 @@ def test_split_item_rows_update_residuals_in_user_order(precision, d, b):
     assert rel_embed_err(W, Wr) <= tol_emb and rel_embed_err(H, Hr) <= tol_emb
 
 
+@pytest.mark.parametrize("precision", [_abi.PREC_FP32, _abi.PREC_BF16])
+def test_relabelled_problem_gives_the_relabelled_result(precision):
+    """Renaming users and items only renames the result (rows of a side are solved
+    independently): the task order, the chunks of long rows, the position map and the
+    user-major residual scan all change with the names, the factors only by rounding.
+    Users without interactions included; every item row is cut into chunks."""
+    d, b = 64, 32
+    rng = np.random.default_rng(90)
+    n_users, n_items = 1500, 300
+    active = np.ones(n_users, bool)
+    active[rng.choice(n_users, 150, replace=False)] = False
+    active[600:640] = False
+    active[0] = active[-1] = False
+    mask = (rng.random((n_users, n_items)) < 0.08) & active[:, None]
+    mask[active, 3] = True
+    u, i = np.nonzero(mask)
+    data = synth.from_pairs(n_users, n_items, u, i)
+    W0, H0 = synth.init_factors(n_users, n_items, d, 0.1 / np.sqrt(d), 90)
+    pu, pi = rng.permutation(n_users), rng.permutation(n_items)
+    users = np.repeat(np.arange(n_users), np.diff(data.u_indptr))
+    data2 = synth.from_pairs(n_users, n_items, pu[users], pi[np.asarray(data.u_items)])
+    W2, H2 = np.empty_like(W0), np.empty_like(H0)
+    W2[pu], H2[pi] = W0, H0
+    m1 = Model(data, d, b, 0.1, 1e-3, 1.0, precision=precision, W0=W0, H0=H0, split_len=32)
+    m2 = Model(data2, d, b, 0.1, 1e-3, 1.0, precision=precision, W0=W2, H0=H2, split_len=32)
+    o1, st1 = m1.epoch(2, objective=True)
+    o2, st2 = m2.epoch(2, objective=True)
+    assert st1 == 0 and st2 == 0
+    Wa, Ha = m1.factors()
+    Wb, Hb = m2.factors()
+    tol = 1e-4 if precision == _abi.PREC_FP32 else 1e-3  # measured 4e-6 / 3e-5: rounding order only
+    print(f"prec={precision}: relabelled W {rel_embed_err(Wb[pu], Wa):.2e} H {rel_embed_err(Hb[pi], Ha):.2e}, "
+          f"objective {abs(o1 - o2) / o1:.2e}")
+    assert rel_embed_err(Wb[pu], Wa) <= tol and rel_embed_err(Hb[pi], Ha) <= tol
+    P = oracle.Problem.from_data(data, d, b, 0.1, 1e-3, 1.0)
+    Wr, Hr, _, _, _ = oracle.ialspp(P, 2, W0, H0)
+    ref = oracle.objective(P, Wr, Hr)
+    obj_tol = OBJ_TOL if precision == _abi.PREC_FP32 else 1e-3
+    assert abs(o1 - ref) <= obj_tol * ref and abs(o2 - ref) <= obj_tol * ref
+
+
 @pytest.mark.parametrize("b,precision", [(16, _abi.PREC_FP32), (64, _abi.PREC_FP32), (32, _abi.PREC_BF16)])
 def test_skewed_user_activity_epochs(b, precision):
     """Zipf(1.3) user activity with rows capped at the whole catalogue (the skewed
